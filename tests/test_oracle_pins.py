@@ -1,0 +1,396 @@
+"""Pins for the FP64 oracle: each checks it against something the paper or the
+mathematics fixes, never against a retyped copy of its own formula."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tilt_oracle as O
+from paper_1205_5351_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_orth(rng, k):
+    q, r = np.linalg.qr(rng.standard_normal((k, k)))
+    return q * np.sign(np.diag(r))
+
+
+# ------------------------------------------------------------------ shrinkage operators
+def test_soft_threshold_closed_form():
+    # T_eps(x) = sgn(x) max(|x| - eps, 0) (Sec. 3.2), values worked by hand
+    x = np.array([-3.0, -1.0, -0.5, 0.0, 0.25, 0.5, 0.75, 2.0])
+    want = np.array([-2.5, -0.5, 0.0, 0.0, 0.0, 0.0, 0.25, 1.5])
+    np.testing.assert_array_equal(O.soft_threshold(x, 0.5), want)
+
+
+def test_soft_threshold_is_l1_prox():
+    # T_eps(y) minimises eps|x| + 1/2 (x - y)^2: brute force on a fine grid
+    grid = np.linspace(-4, 4, 160001)
+    for y in (-2.3, -0.2, 0.0, 0.7, 3.1):
+        f = 0.6 * np.abs(grid) + 0.5 * (grid - y) ** 2
+        assert abs(grid[np.argmin(f)] - O.soft_threshold(np.array(y), 0.6)) < 1e-4
+
+
+def test_svt_of_diagonal_matrix():
+    d = np.array([3.0, 1.2, 0.8, 0.3, 0.0])
+    A, _, s, _ = O.svt(np.diag(d), 0.5)
+    np.testing.assert_allclose(A, np.diag([2.5, 0.7, 0.3, 0.0, 0.0]), atol=1e-14)
+
+
+def test_svt_of_rotated_diagonal():
+    # S_eps(P diag(d) Q^T) = P diag(T_eps(d)) Q^T for orthogonal P, Q (Eq. S_operator)
+    rng = np.random.default_rng(0)
+    P, Q = _rand_orth(rng, 7), _rand_orth(rng, 7)
+    d = np.array([5.0, 2.0, 1.5, 0.9, 0.4, 0.1, 0.05])
+    A, _, _, _ = O.svt(P @ np.diag(d) @ Q.T, 1.0)
+    np.testing.assert_allclose(A, P @ np.diag(np.maximum(d - 1.0, 0)) @ Q.T, atol=1e-12)
+    # rectangular, both orientations: numbers of kept values match
+    R = np.linalg.qr(rng.standard_normal((9, 4)))[0] @ np.diag([4, 3, 0.2, 0.1]) @ _rand_orth(rng, 4)
+    for M in (R, R.T):
+        A, _, _, _ = O.svt(M, 0.5)
+        assert np.linalg.matrix_rank(A, tol=1e-9) == 2
+
+
+def test_svt_is_nuclear_norm_prox():
+    # optimality of A = S_eps(M) for min eps||A||_* + 1/2||A - M||^2:
+    # (M - A)/eps is a subgradient of ||.||_* at A: U_r^T (M-A) V_r = eps I, ||M-A||_2 <= eps
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((12, 8))
+    eps = 1.1
+    A, _, _, _ = O.svt(M, eps)
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    r = int(np.sum(s > 1e-10))
+    G = M - A
+    np.testing.assert_allclose(U[:, :r].T @ G @ Vt[:r].T, eps * np.eye(r), atol=1e-10)
+    assert np.linalg.norm(G, 2) <= eps + 1e-10
+    # and it beats random perturbations
+    f = lambda X: eps * np.linalg.svd(X, compute_uv=False).sum() + 0.5 * np.sum((X - M) ** 2)
+    for _ in range(20):
+        assert f(A) <= f(A + 1e-3 * rng.standard_normal(A.shape)) + 1e-12
+
+
+# ------------------------------------------------------------------ warp (Step 1)
+def test_warp_identity_is_crop():
+    rng = np.random.default_rng(2)
+    img = rng.random((30, 40))
+    m, n = 7, 10   # odd m: integer rows; even n: half-integer columns -> use shifted centre
+    tau = np.array([1.0, 0.0, 20.5, 0.0, 1.0, 13.0])
+    D, _, oob = O.warp(img, tau, O.AFFINE, m, n)
+    # u = j - 4.5, v = i - 3 -> x = j + 16, y = i + 10
+    np.testing.assert_allclose(D, img[10:17, 16:26], atol=1e-15)
+    assert oob == 0
+
+
+def test_bilinear_exact_on_linear_image():
+    # the bilinear interpolant reproduces a linear image exactly, with exact gradients;
+    # x indexes columns and y rows (reading R4)
+    H, W = 40, 50
+    yy, xx = np.mgrid[0:H, 0:W].astype(float)
+    img = 0.3 * xx - 0.7 * yy + 2.0
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, W - 1, 500)
+    y = rng.uniform(0, H - 1, 500)
+    val, gx, gy, oob = O.bilinear(img, x, y)
+    np.testing.assert_allclose(val, 0.3 * x - 0.7 * y + 2.0, atol=1e-12)
+    np.testing.assert_allclose(gx, 0.3, atol=1e-12)
+    np.testing.assert_allclose(gy, -0.7, atol=1e-12)
+    assert not oob.any()
+    # clamped outside, zero derivative along the clamped axis, counted
+    val, gx, gy, oob = O.bilinear(img, np.array([-2.0, 10.0]), np.array([5.0, 45.0]))
+    np.testing.assert_allclose(val, [0.3 * 0 - 0.7 * 5 + 2, 0.3 * 10 - 0.7 * 39 + 2])
+    np.testing.assert_allclose(gx, [0.0, 0.3])
+    np.testing.assert_allclose(gy, [-0.7, 0.0])
+    assert oob.tolist() == [True, True]
+
+
+def _fd_jacobian(img, tau, ttype, m, n, h):
+    cols = []
+    for k in range(ttype):
+        e = np.zeros(ttype)
+        e[k] = h[k]
+        Dp, _, _, _ = O.warp_normalise_jacobian(img, tau + e, ttype, m, n)
+        Dm, _, _, _ = O.warp_normalise_jacobian(img, tau - e, ttype, m, n)
+        cols.append(((Dp - Dm) / (2 * h[k])).ravel())
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("ttype", [O.AFFINE, O.PROJECTIVE])
+def test_jacobian_matches_central_differences(ttype):
+    # J = d/dzeta (D o zeta / ||D o zeta||_F) (Algorithm 1, Step 1) vs central differences;
+    # tau chosen so that no sample is within 1e-4 px of a cell boundary (the bilinear
+    # interpolant has kinks there)
+    p = synth.small_affine()
+    m, n = 30, 34
+    U, V = O.window_uv(m, n)
+    for shift in np.arange(20) * 0.0371:
+        base = np.array([0.9713, -0.1687, 53.217 + shift, 0.2291, 1.0377, 52.861 - shift])
+        tau = base if ttype == O.AFFINE else np.r_[base, 3.1e-4, -2.3e-4]
+        x, y, _, _ = O.map_points(tau, ttype, U, V)
+        if np.minimum(np.abs(x - np.round(x)), np.abs(y - np.round(y))).min() > 1e-4:
+            break
+    else:
+        raise AssertionError("no kink-free tau found")
+    _, J, _, _ = O.warp_normalise_jacobian(p.img, tau, ttype, m, n)
+    h = np.full(ttype, 1e-7)
+    if ttype == O.PROJECTIVE:
+        h[6:] = 1e-10
+    Jfd = _fd_jacobian(p.img, tau, ttype, m, n, h)
+    for k in range(ttype):
+        assert np.linalg.norm(Jfd[:, k] - J[:, k]) <= 1e-6 * np.linalg.norm(J[:, k]), k
+    # the normalised warp's Jacobian is orthogonal to D_hat (its norm is constant)
+    Dhat, _, _, _ = O.warp_normalise_jacobian(p.img, tau, ttype, m, n)
+    assert np.abs(Dhat.ravel() @ J).max() < 1e-12 * np.abs(J).max() * m * n
+
+
+# ------------------------------------------------------------------ constraints Q
+@pytest.mark.parametrize("ttype", [O.AFFINE, O.PROJECTIVE])
+def test_constraint_rows_are_derivatives_of_centroid_and_area(ttype):
+    m, n = 21, 30
+    base = np.array([0.95, 0.12, 40.3, -0.2, 1.07, 33.9])
+    tau = base if ttype == O.AFFINE else np.r_[base, 4e-4, -6e-4]
+    Q = O.constraint_rows(tau, ttype, m, n)
+
+    def geom(t):
+        U, V = O.corner_uv(m, n)
+        x, y, _, _ = O.map_points(t, ttype, U, V)
+        return np.array([x.mean(), y.mean(), O.polygon_area(x, y) / ((m - 1) * (n - 1))])
+
+    h = 1e-6
+    for k in range(ttype):
+        e = np.zeros(ttype)
+        e[k] = h
+        fd = (geom(tau + e) - geom(tau - e)) / (2 * h)
+        np.testing.assert_allclose(Q[:, k], fd, rtol=1e-6, atol=1e-7)
+    # the unit-square-normalised area of the identity window is 1
+    U, V = O.corner_uv(m, n)
+    x, y, _, _ = O.map_points(np.array([1, 0, 5, 0, 1, 7.0]), O.AFFINE, U, V)
+    assert abs(abs(O.polygon_area(x, y)) - (m - 1) * (n - 1)) < 1e-9
+
+
+# ------------------------------------------------------------------ J_perp and W^T W
+def test_jperp_symmetric_idempotent_unit_norm():
+    # Eq. J_properties and Proposition 2, with J_perp formed explicitly from the operator
+    rng = np.random.default_rng(4)
+    J = rng.standard_normal((40, 6))
+    op = O.WtW(J, None)
+    P = np.stack([op(e) for e in np.eye(40)], axis=1)
+    np.testing.assert_allclose(P, P.T, atol=1e-13)
+    np.testing.assert_allclose(P @ P, P, atol=1e-13)
+    assert abs(np.linalg.norm(P, 2) - 1.0) < 1e-12
+    np.testing.assert_allclose(P @ J, 0, atol=1e-12)       # null(J_perp) = span(J)
+    assert np.linalg.matrix_rank(P) == 40 - 6
+
+
+def test_wtw_property_against_explicit_w():
+    # W = [I - J G^{-1} J^T ; -Q G^{-1} J^T] with G = J^T J + Q^T Q (Sec. 4.3);
+    # Eq. WTW_property: W^T W = I - J G^{-1} J^T, and ||W||_2 = 1
+    rng = np.random.default_rng(5)
+    S, p, l = 30, 6, 3
+    J = rng.standard_normal((S, p))
+    Q = rng.standard_normal((l, p))
+    G = J.T @ J + Q.T @ Q
+    W = np.vstack([np.eye(S) - J @ np.linalg.solve(G, J.T), -Q @ np.linalg.solve(G, J.T)])
+    op = O.WtW(J, Q)
+    WtW = np.stack([op(e) for e in np.eye(S)], axis=1)
+    np.testing.assert_allclose(W.T @ W, WtW, atol=1e-12)
+    assert abs(np.linalg.norm(W, 2) - 1.0) < 1e-12
+    # not idempotent when Q != 0: (W^T W)^2 = W^T W - J G^{-1} Q^T Q G^{-1} J^T
+    Gi = np.linalg.inv(G)
+    np.testing.assert_allclose(WtW @ WtW, WtW - J @ Gi @ Q.T @ Q @ Gi @ J.T, atol=1e-12)
+    assert np.abs(WtW @ WtW - WtW).max() > 1e-6
+    # the constraint set: W r = 0  <=>  r = J dtau with Q dtau = 0 (Proposition 1, Sec. 4.3)
+    N = np.linalg.svd(Q)[2][l:].T            # basis of null(Q)
+    r = J @ (N @ rng.standard_normal(p - l))
+    np.testing.assert_allclose(W @ r, 0, atol=1e-12)
+
+
+def test_delta_tau_solves_stacked_system():
+    # Eq. two_linear_constraint: [J; Q] dtau = [A + E - D; 0] in the least-squares sense,
+    # solved here by LAPACK's lstsq on the stacked matrix
+    rng = np.random.default_rng(6)
+    m, n, p = 8, 9, 8
+    J = rng.standard_normal((m * n, p))
+    Q = rng.standard_normal((3, p))
+    A, E, D = (rng.standard_normal((m, n)) for _ in range(3))
+    dt = O.delta_tau(O.WtW(J, Q), A, E, D)
+    ref = np.linalg.lstsq(np.vstack([J, Q]), np.r_[(A + E - D).ravel(), np.zeros(3)], rcond=None)[0]
+    np.testing.assert_allclose(dt, ref, rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------------------ inner loop
+def _tilt_inner_case(seed=7, m=40, n=36, ttype=O.AFFINE):
+    p = synth.make_patch(np.random.default_rng(seed), m, n, kind="lowrank", rank=2, theta_deg=6.0,
+                         corruption=0.05, ttype=ttype)
+    tau = p.tau0 + (np.r_[0.011, -0.007, 0.3, 0.005, 0.013, -0.2, 0, 0][:ttype])
+    Dhat, J, _, _ = O.warp_normalise_jacobian(p.img, tau, ttype, m, n)
+    Q = O.constraint_rows(tau, ttype, m, n)
+    return Dhat, J, Q
+
+
+def test_inner_invariants_and_kkt():
+    Dhat, J, Q = _tilt_inner_case()
+    m, n = Dhat.shape
+    lam = 1 / math.sqrt(max(m, n))
+    # Cond2 bounds the dual residual, so the KKT conditions hold to about eps2 at exit
+    prm = O.Params(eps1=1e-10, eps2=1e-4, max_inner=20000)
+    tol = prm.eps2
+    res = O.inner_ladmap(Dhat, J, Q, lam, Dhat, np.zeros_like(Dhat), np.zeros_like(Dhat), prm)
+    assert res.converged
+    mus = np.array(res.mu_trace)
+    assert np.all(np.diff(mus) >= 0) and mus.max() <= prm.mu_max          # Eq. mu
+    op = O.WtW(J, Q)
+    d0 = np.linalg.norm(op(Dhat))
+    assert np.linalg.norm(op(res.A + res.E - Dhat)) / d0 < prm.eps1       # Eq. Cond1
+    # KKT (with the +mu multiplier sign): -Yt in d||A||_* and -Yt in lam d||E||_1
+    Yt = res.Yt
+    U, s, Vt = np.linalg.svd(res.A, full_matrices=False)
+    r = int(np.sum(s > 1e-6 * s[0]))
+    assert np.linalg.norm(Yt, 2) <= 1 + tol
+    np.testing.assert_allclose(U[:, :r].T @ (-Yt) @ Vt[:r].T, np.eye(r), atol=tol)
+    supp = np.abs(res.E) > 1e-9
+    assert supp.sum() > 0
+    np.testing.assert_allclose(-Yt[supp], lam * np.sign(res.E[supp]), atol=tol * lam)
+    assert np.abs(Yt[~supp]).max() <= lam * (1 + tol)
+    # Proposition 1: D_hat + J dtau = A + E at the optimum, and Q dtau = 0
+    dt = O.delta_tau(op, res.A, res.E, Dhat)
+    assert np.linalg.norm(Dhat.ravel() + J @ dt - (res.A + res.E).ravel()) < 1e-7
+    assert np.linalg.norm(Q @ dt) < 1e-7 * max(1.0, np.linalg.norm(dt))
+
+
+def test_inner_y_stays_in_span_of_jperp():
+    # Sec. 4.2: with Q = 0 and Y_0 in span(J_perp), every Y_k stays there (J^T Y_k = 0)
+    Dhat, J, _ = _tilt_inner_case(seed=8)
+    lam = 1 / math.sqrt(max(Dhat.shape))
+    trace_Y = []
+    prm = O.Params(max_inner=30, eps1=0.0)
+    rng = np.random.default_rng(0)
+    Y0 = rng.standard_normal(Dhat.shape)
+    for k in (1, 5, 30):
+        prm.max_inner = k
+        res = O.inner_ladmap(Dhat, J, None, lam, Dhat, np.zeros_like(Dhat), Y0, prm)
+        trace_Y.append(np.abs(J.T @ res.Yt.ravel()).max() / np.abs(res.Yt).max())
+    assert max(trace_Y) < 1e-10
+
+
+def test_rpca_special_case_exact_recovery():
+    # with no Jacobian the inner problem is RPCA: a rank-3 + 5 % sparse 50 x 50 matrix is
+    # recovered exactly with lambda = 1/sqrt(50)
+    rng = np.random.default_rng(9)
+    m = n = 50
+    L = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n)) / math.sqrt(n)
+    S = np.zeros((m, n))
+    mask = rng.random((m, n)) < 0.05
+    S[mask] = rng.uniform(-1, 1, mask.sum())
+    D = L + S
+    prm = O.Params(eps1=1e-10, eps2=1e-2, max_inner=5000)
+    res = O.inner_ladmap(D, np.zeros((m * n, 0)), None, 1 / math.sqrt(50), D, 0 * D, 0 * D, prm)
+    assert res.converged
+    assert np.linalg.norm(res.A - L) / np.linalg.norm(L) < 1e-6
+    assert np.linalg.norm(res.E - S) / np.linalg.norm(S) < 1e-6
+
+
+@pytest.mark.parametrize("size", [50, 100])
+def test_table_numerical_objective(size):
+    # Table 1: the inner loop on random D o tau and J stops at the printed objective.
+    # 10 trials with D o tau ~ U[-1/2, 1/2], J ~ N(0, 1), lambda = 1/sqrt(n), p = 6.
+    rows = json.load(open(os.path.join(GOLDEN, "table_numerical.json")))["rows"]
+    want = {r[0]: r[2] for r in rows}[size]
+    prm = O.Params(eps1=1e-7, eps2=1e-2, max_inner=2000)
+    objs = []
+    for trial in range(10):
+        rng = np.random.default_rng(1000 + trial)
+        D, J = synth.random_inner_problem(rng, size, size, 6)
+        D = D - 0.5
+        lam = 1 / math.sqrt(size)
+        res = O.inner_ladmap(D, J, None, lam, D, 0 * D, 0 * D, prm)
+        objs.append(O.objective(res.A, res.E, lam))
+    assert abs(np.mean(objs) - want) / want < 0.01
+
+
+# ------------------------------------------------------------------ Algorithm 1 end to end
+def _offdiag(tau, tau_true):
+    L = np.array([[tau_true[0], tau_true[1]], [tau_true[3], tau_true[4]]])
+    T = np.array([[tau[0], tau[1]], [tau[3], tau[4]]])
+    X = np.linalg.solve(L, T)    # diagonal when tau = tau_true up to axis scaling
+    return abs(X[0, 1]) / abs(X[0, 0]) + abs(X[1, 0]) / abs(X[1, 1])
+
+
+@pytest.mark.parametrize("seed,m,theta,rank", [(0, 24, 6.0, 2), (1, 32, 8.0, 2), (2, 32, 8.0, 1)])
+def test_tilt_recovers_known_rotation(seed, m, theta, rank):
+    # a rank-r texture rendered under a known rotation is rectified: tau matches tau_G up
+    # to the axis scalings that leave a separable texture low-rank, and D_hat(tau*) has
+    # numerical rank r + 1 (texture plus the constant of the [0, 1] rescale)
+    p = synth.make_patch(np.random.default_rng(seed), m, m, kind="lowrank", rank=rank,
+                         cell=m / 4, theta_deg=theta)
+    res = O.tilt(p.img, p.tau0, O.AFFINE, m, m, O.Params(max_outer=30, outer_tol=1e-4))
+    assert _offdiag(res.tau, p.tau_true) < 1e-2
+    Dhat, _, _, _ = O.warp_normalise_jacobian(p.img, res.tau, O.AFFINE, m, m)
+    s = np.linalg.svd(Dhat, compute_uv=False)
+    assert s[rank + 1] < 3e-3 * s[0]
+
+
+def test_rotation_grid_minimum_at_true_angle():
+    # exhaustive search over the rotation angle in 0.25 deg steps: the nuclear norm of the
+    # normalised warp is smallest at the angle used to render the texture
+    p = synth.make_patch(np.random.default_rng(3), 32, 32, kind="lowrank", rank=2, cell=8,
+                         theta_deg=7.0)
+    cx, cy = p.tau0[2], p.tau0[5]
+    angles = np.arange(0.0, 14.01, 0.25)
+    nuc = []
+    for a in angles:
+        tau = synth.tau_vector(synth.linear_part(a, 0.0), cx, cy)
+        Dhat, _, _, _ = O.warp_normalise_jacobian(p.img, tau, O.AFFINE, 32, 32)
+        nuc.append(np.linalg.svd(Dhat, compute_uv=False).sum())
+    assert abs(angles[int(np.argmin(nuc))] - 7.0) <= 0.5
+
+
+# ------------------------------------------------------------------ Algorithm 2 (Appendix A)
+def _svd_case(seed=11, m=9, n=6):
+    rng = np.random.default_rng(seed)
+    M0 = rng.standard_normal((m, n))
+    U, s, Vt = np.linalg.svd(M0, full_matrices=False)
+    M = M0 + 0.05 * rng.standard_normal((m, n))
+    return M, U, s, Vt.T
+
+
+def test_cayley_curve_properties():
+    # Sec. 5.1: X(t)^T X(t) = I, X(0) = X, X'(0) = -P
+    M, U, S, V = _svd_case()
+    PU, PS, PV, _, _ = O.svdws_derivatives(M, U, S, V)
+    for t in (0.0, 0.3, -1.7):
+        Ut = O.cayley(PU, U, t)
+        np.testing.assert_allclose(Ut.T @ Ut, np.eye(U.shape[1]), atol=1e-12)
+    np.testing.assert_allclose(O.cayley(PU, U, 0.0), U, atol=1e-15)
+    h = 1e-6
+    d = (O.cayley(PU, U, h) - O.cayley(PU, U, -h)) / (2 * h)
+    np.testing.assert_allclose(d, -PU @ U, atol=1e-7)
+
+
+def test_svdws_derivatives_match_finite_differences():
+    # Appendix A: f'(0) and f''(0) of f(t) = 1/2||M - U(t) Sigma(t) V(t)^T||^2
+    M, U, S, V = _svd_case()
+    PU, PS, PV, f1, f2 = O.svdws_derivatives(M, U, S, V)
+    f = lambda t: O.curve_objective(M, *O.curve_point(M, U, S, V, PU, PS, PV, t))
+    h = 1e-4
+    assert abs((f(h) - f(-h)) / (2 * h) - f1) < 1e-6 * max(1, abs(f1))
+    assert abs((f(h) - 2 * f(0) + f(-h)) / h**2 - f2) < 1e-4 * max(1, abs(f2))
+
+
+def test_svdws_accuracy_bound():
+    # Sec. 5.2: ||S_eps(U~ S~ V~^T) - S_eps(M_k)||_F <= ||M_{k-1} - M_k||_F
+    rng = np.random.default_rng(12)
+    for trial in range(5):
+        Mprev = rng.standard_normal((10, 7))
+        U, s, Vt = np.linalg.svd(Mprev, full_matrices=False)
+        M = Mprev + 0.02 * rng.standard_normal(Mprev.shape)
+        ws = O.svd_warm_start(M, U, s, Vt.T)
+        assert ws is not None
+        approx = (ws[0] * ws[1]) @ ws[2].T
+        for eps in (0.1, 0.5, 1.0):
+            lhs = np.linalg.norm(O.svt(approx, eps)[0] - O.svt(M, eps)[0])
+            assert lhs <= np.linalg.norm(Mprev - M) + 1e-12
+        # the step decreases f
+        assert O.curve_objective(M, *ws) <= O.curve_objective(M, U, s, Vt.T)
