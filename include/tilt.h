@@ -1,0 +1,199 @@
+/*
+ * tilt.h -- C ABI of the GB300 (sm_103a) solver for Transform Invariant Low-rank Textures
+ * by the Linearized Alternating Direction Method with Adaptive Penalty and warm starts
+ * (Ren & Lin, arXiv 1205.5351).
+ *
+ * The solver rectifies an m x n window of an image: it finds the transform tau (affine,
+ * p = 6, or projective, p = 8) and the split D o tau / ||D o tau||_F = A + E with A of low
+ * rank and E sparse, by Algorithm 1 of the paper (outer loop: warp, normalise, Jacobian,
+ * dtau; inner loop: LADMAP on the reformulated problem of Sec. 3.2 / 4.3 with singular
+ * value thresholding, soft thresholding, the multiplier update and the adaptive penalty).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images are float32, row-major, element (row y, column x) at img[y * ld + x], H >= 2,
+ * W >= 2.  Window pixel (i, j), 0 <= i < m, 0 <= j < n, has centred coordinates
+ * u = j - (n-1)/2, v = i - (m-1)/2.  tau maps (u, v) to image coordinates (x = column,
+ * y = row):
+ *   affine      tau = [a11 a12 a13 a21 a22 a23]:  x = a11 u + a12 v + a13,
+ *                                                 y = a21 u + a22 v + a23
+ *   projective  tau = [h1 .. h8]:  x = (h1 u + h2 v + h3) / (h7 u + h8 v + 1),
+ *                                  y = (h4 u + h5 v + h6) / (h7 u + h8 v + 1)
+ * D o tau is the bilinear interpolant of the image at those points; coordinates outside
+ * the image are clamped to the edge (and counted).  Window sides: 2 <= m, n <= 512.
+ *
+ * Return codes are tilt_status values; on a negative code tilt_last_error() returns a
+ * message for the calling thread.  No entry point is thread-safe on one context; use one
+ * context per host thread.
+ */
+#ifndef TILT_H
+#define TILT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tilt_ctx tilt_ctx;
+
+typedef enum { TILT_AFFINE = 6, TILT_PROJECTIVE = 8 } tilt_transform;
+
+typedef enum {
+    TILT_OK = 0,
+    TILT_PENDING = 1,       /* tilt_poll: the problem has not finished yet                    */
+    TILT_E_INVAL = -1,      /* an argument is out of range                                    */
+    TILT_E_NOMEM = -2,      /* the problem can never fit the context's device-memory budget  */
+    TILT_E_BUSY = -3,       /* the admission queue is full; retry after polling              */
+    TILT_E_CUDA = -4,       /* a CUDA call failed (message has the CUDA error string)         */
+    TILT_E_TIMEOUT = -5,    /* a bounded wait expired                                         */
+    TILT_E_NOTFOUND = -6    /* unknown or already retired ticket                              */
+} tilt_status;
+
+/* Context configuration.  Zero-initialise and set what you need. */
+typedef struct {
+    int device;                 /* CUDA device ordinal                                        */
+    size_t hbm_budget_bytes;    /* device workspace pool; 0 -> 25 % of free memory at create  */
+    int max_live;               /* problems admitted at once; 0 -> 65536                      */
+    void* cuda_stream;          /* reserved; the context always creates its own streams       */
+    const char* autotune_cache; /* reserved                                                   */
+} tilt_config;
+
+/* Solver parameters (Algorithm 1 inputs).  tilt_default_params() fills the defaults;
+ * a value <= 0 in lambda or mu0 selects the default rule. */
+typedef struct {
+    double lambda;     /* weight of ||E||_1; <= 0 -> 1/sqrt(max(m, n))                        */
+    double eps1;       /* Eq. Cond1 threshold (default 1e-6)                                  */
+    double eps2;       /* Eq. Cond2 / Eq. rho threshold (default 0.1)                         */
+    double rho0;       /* Eq. rho growth factor, >= 1 (default 1.5)                           */
+    double mu0;        /* initial penalty of every inner loop; <= 0 -> 1.25 / ||D_hat||_2     */
+    double mu_max;     /* Eq. mu upper bound (default 1e10)                                   */
+    double eps_svd;    /* SVD warm-start gate (Alg. 2): warm when ||M_k - M_k-1||_F <
+                          eps_svd * ||M_k||_F (default 0.05); < 0 -> always warm             */
+    int max_inner;     /* inner iterations per outer step (default 500)                       */
+    int max_outer;     /* outer steps (default 10)                                            */
+    double outer_tol;  /* stop when dtau moves no window corner by more than this many
+                          pixels (default 1e-2)                                               */
+} tilt_params;
+
+/* Result of one problem. */
+typedef struct {
+    int status;          /* 0 outer loop converged, 1 max_outer reached, 2 some inner loop hit
+                            max_inner (tau still valid), < 0 numeric failure (-1 non-finite,
+                            -2 singular J^T J + Q^T Q, -3 zero image window)                  */
+    int p;               /* 6 or 8                                                             */
+    double tau[8];       /* final transform (first p entries)                                 */
+    double objective;    /* ||A||_* + lambda ||E||_1 of the last inner loop (Eq. TILT_2)       */
+    double lambda;       /* lambda actually used                                              */
+    int rank_A;          /* singular values of A above 1e-3 * the largest                     */
+    int outer_iters;     /* outer steps taken                                                 */
+    int inner_iters;     /* inner iterations summed over outer steps                          */
+    int svd_sweeps;      /* one-sided Jacobi sweeps summed over all SVDs                      */
+    int svd_warm;        /* SVDs that started from the previous right singular vectors        */
+    int oob_pixels;      /* samples clamped to the image edge in the last warp                */
+    double kkt_residual; /* last Eq. Cond1 value                                              */
+    float latency_ms;    /* submit -> completion, host clock                                  */
+} tilt_result;
+
+/* Fill *p with the default parameters. */
+void tilt_default_params(tilt_params* p);
+
+/* Create a context on cfg->device: allocates the device workspace pool (budget), its
+ * streams and pinned completion records.  *out receives the context.  Errors:
+ * TILT_E_INVAL (null pointer, bad device), TILT_E_CUDA. */
+int tilt_create(const tilt_config* cfg, tilt_ctx** out);
+
+/* Queue one problem (Algorithm 1 input: window D given by the image and m x n, initial
+ * transform tau0[p], transform type, parameters; params may be NULL for defaults).
+ * img is a host pointer (is_device_ptr = 0; copied before the call returns, so the caller
+ * may reuse it at once) or a device pointer (is_device_ptr = 1; it must stay valid and
+ * unchanged until the problem retires).  ld_elems is the image row stride in elements.
+ * The problem starts on the GPU at once when it fits the budget, otherwise when earlier
+ * problems retire.  *ticket_out identifies it for tilt_poll.  Errors: TILT_E_INVAL,
+ * TILT_E_NOMEM (larger than the whole budget), TILT_E_BUSY (max_live reached), TILT_E_CUDA. */
+int tilt_submit(tilt_ctx* ctx, const float* img, int H, int W, size_t ld_elems, int is_device_ptr,
+                int m, int n, const double* tau0, tilt_transform type, const tilt_params* params,
+                uint64_t* ticket_out);
+
+/* One problem of a grouped submission. */
+typedef struct {
+    const float* img;    /* host or device pointer (see is_device_ptr of tilt_submit_batch)  */
+    int H, W;
+    size_t ld_elems;
+    int m, n;
+    int type;            /* tilt_transform                                                    */
+    double tau0[8];
+} tilt_problem;
+
+/* Queue count problems as one grouped launch per size class (problems ordered by cost,
+ * largest first, so that the block scheduler balances the load).  Same semantics as
+ * count calls of tilt_submit; tickets_out[count] receives the tickets.  Either every
+ * problem is admitted or none is (TILT_E_NOMEM / TILT_E_BUSY). */
+int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, int is_device_ptr,
+                      const tilt_params* params, uint64_t* tickets_out);
+
+/* Non-blocking completion check.  TILT_PENDING while running; TILT_OK once finished, in
+ * which case *out (if non-NULL) receives the result, A_out / E_out (host, m x n row-major,
+ * may be NULL) receive the final low-rank texture and sparse error of the normalised
+ * window, and the ticket is retired (TILT_E_NOTFOUND afterwards).  Nothing is written
+ * while the problem is pending. */
+int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, float* E_out);
+
+/* Blocking form of tilt_poll: waits up to timeout_ms (< 0: 60 s) and returns TILT_E_TIMEOUT
+ * if the problem is still running then. */
+int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, float* A_out,
+              float* E_out);
+
+/* Wait (bounded, 120 s) for all work, free everything.  Returns TILT_E_TIMEOUT if work was
+ * still running when the wait expired (resources are then leaked, never freed under a
+ * running kernel). */
+int tilt_destroy(tilt_ctx* ctx);
+
+/* Message of the last error on the calling thread ("" if none).  ctx is unused. */
+const char* tilt_last_error(tilt_ctx* ctx);
+
+/* Number of device kernels this context has launched (for launch accounting). */
+uint64_t tilt_kernel_launches(tilt_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------------
+ * Step-level entry points.  They run one step of the method on one problem with the same
+ * device code the solver uses, on the context's stream, and return when it has finished.
+ * Device planes (m x n) are stored long-side contiguous: element (i, j) at j*m + i when
+ * m >= n and at i*n + j when m < n.  J is p such planes back to back.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Algorithm 1 Step 1: D_hat = D o tau / ||D o tau||_F and the Jacobian J of the normalised
+ * warp w.r.t. tau (quotient rule).  img_dev: device image; Dhat_dev (m*n) and J_dev (p*m*n)
+ * device outputs.  *norm_out = ||D o tau||_F, *oob_out = clamped samples (both may be NULL). */
+int tilt_warp_jacobian(tilt_ctx* ctx, const float* img_dev, int H, int W, size_t ld_elems, int m,
+                       int n, const double* tau, tilt_transform type, float* Dhat_dev, float* J_dev,
+                       double* norm_out, int* oob_out);
+
+/* Sec. 4.3: Q (3 x p: linearised centroid x, centroid y and signed area of the window
+ * corners mapped by tau, the area row divided by (m-1)(n-1)), G = J^T J + Q^T Q and G^-1,
+ * all row-major host outputs (any may be NULL), computed in FP64 on the device. */
+int tilt_gram(tilt_ctx* ctx, const float* J_dev, int m, int n, const double* tau, tilt_transform type,
+              double* Q_out, double* G_out, double* Ginv_out);
+
+/* Eqs. A_1, S_operator: A = U max(Sigma - eps, 0) V^T for the m x n device matrix M_dev
+ * (layout above) by one-sided Jacobi.  A_dev receives A; sigma_out (host, min(m, n), may be
+ * NULL) the singular values of M in no particular order; *sweeps_out the sweeps used. */
+int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* A_dev,
+             float* sigma_out, int* sweeps_out);
+
+/* The inner loop of Algorithm 1 (Eqs. A, E, Y, mu, rho, Cond1, Cond2 in the W^T W form of
+ * Eq. newvars2) on given D_hat, J and tau (tau gives Q).  A_dev, E_dev, Y_dev are the warm
+ * start on entry (Y is projected by W^T W first, Eq. Y_new_warmstart) and the result on
+ * exit.  mu0 <= 0 -> 1.25 / ||D_hat||_2.  Outputs (host, may be NULL): *iters_out,
+ * dtau_out[p] (Eq. Delta_tau with Q), *c1_out, *c2_out, *mu_out (last mu used). */
+int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, int n,
+               const double* tau, tilt_transform type, const tilt_params* params, double mu0,
+               float* A_dev, float* E_dev, float* Y_dev, int* iters_out, double* dtau_out,
+               double* c1_out, double* c2_out, double* mu_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TILT_H */

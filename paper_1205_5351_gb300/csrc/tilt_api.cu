@@ -1,0 +1,785 @@
+// Host runtime of the C ABI declared in include/tilt.h: context, device-memory pool,
+// admission, grouped launches, completion tracking.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tilt.h"
+#include "tilt_launch.h"
+
+using namespace tilt;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(TILT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+// First-fit allocator over [0, size) with coalescing free blocks.
+class Pool {
+public:
+    void init(size_t size) { free_.clear(); free_[0] = size; size_ = size; used_ = 0; }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = align_up(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = align_up(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+
+private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0, used_ = 0;
+};
+
+struct Layout {   // byte offsets inside one problem's workspace
+    size_t dhat, j, a, e, y, p, mp, bg, vg, tg, img, order, total;
+    int smem_svd, minb;
+    size_t smem;
+};
+
+struct Request {   // one problem as submitted
+    const float* img;
+    int H, W;
+    size_t ld;
+    int is_dev;
+    int m, n, p;
+    double tau0[8];
+    Params prm;
+    std::vector<float> host_copy;   // owned copy while waiting for admission
+};
+
+struct Ticket {
+    int slot = -1;               // -1: waiting for admission
+    size_t ws_off = 0, ws_bytes = 0;
+    Layout lay{};
+    int m = 0, n = 0, p = 0;
+    double t_submit = 0, t_done = 0;
+    int batch = -1;              // owning grouped launch (order-array lifetime)
+    Request req;
+};
+
+struct Batch {
+    size_t off = 0, bytes = 0;
+    int live = 0;
+};
+
+}  // namespace
+
+struct tilt_ctx {
+    int device = 0;
+    int max_live = 0;
+    size_t max_smem = 0;
+    cudaStream_t streams[4] = {};
+    cudaStream_t copy_stream = nullptr;
+    int next_stream = 0;
+    char* pool_base = nullptr;
+    Pool pool;
+    Problem* probs = nullptr;       // host-mapped
+    Problem* probs_dev = nullptr;
+    Result* res = nullptr;
+    Result* res_dev = nullptr;
+    int* done = nullptr;
+    int* done_dev = nullptr;
+    std::vector<int> free_slots;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    std::deque<uint64_t> waiting;   // admitted in FIFO order when memory frees up
+    std::unordered_map<int, Batch> batches;
+    int next_batch = 0;
+    uint64_t next_ticket = 1;
+    uint64_t launches = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    StepOut* step_out = nullptr;    // host-mapped
+    StepOut* step_out_dev = nullptr;
+};
+
+namespace {
+
+Params to_params(const tilt_params* p) {
+    tilt_params d;
+    tilt_default_params(&d);
+    if (!p) p = &d;
+    Params q;
+    q.lam = p->lambda;
+    q.eps1 = p->eps1;
+    q.eps2 = p->eps2;
+    q.rho0 = p->rho0;
+    q.mu0 = p->mu0;
+    q.mu_max = p->mu_max;
+    q.eps_svd = p->eps_svd;
+    q.outer_tol = p->outer_tol;
+    q.max_inner = p->max_inner;
+    q.max_outer = p->max_outer;
+    return q;
+}
+
+bool params_ok(const Params& q) {
+    return q.eps1 >= 0 && q.eps2 >= 0 && q.rho0 >= 1.0 && q.mu_max > 0 && q.max_inner >= 1 && q.max_outer >= 1 &&
+           q.outer_tol >= 0 && std::isfinite(q.lam) && std::isfinite(q.mu0);
+}
+
+Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_img) {
+    Layout L{};
+    const Dims d = make_dims(m, n, p);
+    const size_t S = (size_t)d.S * sizeof(float);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += align_up(bytes); return r; };
+    L.dhat = take(S);
+    L.j = take(S * p);
+    L.a = take(S);
+    L.e = take(S);
+    L.y = take(S);
+    L.p = take(S);
+    L.mp = take(S);
+    const size_t svd = svd_smem_bytes(d);
+    const size_t head = smem_head_bytes();
+    L.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    if (L.smem_svd) {
+        L.bg = L.vg = L.tg = 0;
+        L.smem = svd + head;
+        L.minb = (L.smem <= 100 * 1024) ? 2 : 1;
+    } else {
+        const size_t nb = (size_t)d.ldb * d.Cp * sizeof(float), nv = (size_t)d.ldv * d.Cp * sizeof(float);
+        L.bg = take(nb);
+        L.vg = take(nv);
+        L.tg = take(nb);
+        L.smem = head;
+        L.minb = 1;
+    }
+    L.img = copy_img ? take((size_t)H * W * sizeof(float)) : 0;
+    L.order = take(sizeof(int));
+    L.total = o;
+    return L;
+}
+
+int validate(int H, int W, size_t ld, int m, int n, int type, const float* img) {
+    if (!img) return fail(TILT_E_INVAL, "null image");
+    if (H < 2 || W < 2) return fail(TILT_E_INVAL, "image must be at least 2 x 2 (got %d x %d)", H, W);
+    if (ld < (size_t)W) return fail(TILT_E_INVAL, "ld_elems %zu < W %d", ld, W);
+    if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE)
+        return fail(TILT_E_INVAL, "window %d x %d outside 2..%d", m, n, MAX_SIDE);
+    if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "bad transform type %d", type);
+    return TILT_OK;
+}
+
+// Fill the descriptor of an admitted ticket and upload its image (host case).
+int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
+    char* base = ctx->pool_base + t.ws_off;
+    Problem& pr = ctx->probs[t.slot];
+    const Request& rq = t.req;
+    const Layout& L = t.lay;
+    memset(&pr, 0, sizeof pr);
+    if (rq.is_dev) {
+        pr.img = rq.img;
+        pr.ld = (long long)rq.ld;
+    } else {
+        float* dimg = reinterpret_cast<float*>(base + L.img);
+        const float* src = rq.host_copy.empty() ? rq.img : rq.host_copy.data();
+        const size_t lds = rq.host_copy.empty() ? rq.ld : (size_t)rq.W;
+        CUDA_TRY(cudaMemcpy2DAsync(dimg, rq.W * sizeof(float), src, lds * sizeof(float), rq.W * sizeof(float), rq.H,
+                                   cudaMemcpyHostToDevice, st));
+        pr.img = dimg;
+        pr.ld = rq.W;
+    }
+    pr.H = rq.H;
+    pr.W = rq.W;
+    pr.m = rq.m;
+    pr.n = rq.n;
+    pr.p = rq.p;
+    pr.ttype = rq.p;
+    for (int k = 0; k < 8; ++k) pr.tau[k] = k < rq.p ? rq.tau0[k] : 0.0;
+    pr.prm = rq.prm;
+    pr.pl.Dhat = reinterpret_cast<float*>(base + L.dhat);
+    pr.pl.J = reinterpret_cast<float*>(base + L.j);
+    pr.pl.A = reinterpret_cast<float*>(base + L.a);
+    pr.pl.E = reinterpret_cast<float*>(base + L.e);
+    pr.pl.Y = reinterpret_cast<float*>(base + L.y);
+    pr.pl.P = reinterpret_cast<float*>(base + L.p);
+    pr.pl.Mp = reinterpret_cast<float*>(base + L.mp);
+    if (!L.smem_svd) {
+        pr.pl.Bg = reinterpret_cast<float*>(base + L.bg);
+        pr.pl.Vg = reinterpret_cast<float*>(base + L.vg);
+        pr.pl.Tg = reinterpret_cast<float*>(base + L.tg);
+    }
+    pr.smem_svd = L.smem_svd;
+    pr.res = ctx->res_dev + t.slot;
+    pr.done = ctx->done_dev + t.slot;
+    ctx->done[t.slot] = 0;
+    return TILT_OK;
+}
+
+void release_ticket(tilt_ctx* ctx, uint64_t id) {
+    auto it = ctx->tickets.find(id);
+    if (it == ctx->tickets.end()) return;
+    Ticket& t = it->second;
+    if (t.slot >= 0) {
+        ctx->pool.release(t.ws_off, t.ws_bytes);
+        ctx->free_slots.push_back(t.slot);
+    }
+    if (t.batch >= 0) {
+        auto b = ctx->batches.find(t.batch);
+        if (b != ctx->batches.end() && --b->second.live == 0) {
+            ctx->pool.release(b->second.off, b->second.bytes);
+            ctx->batches.erase(b);
+        }
+    }
+    ctx->tickets.erase(it);
+}
+
+// Admit as many waiting requests as fit, each as its own launch.
+int admit_waiting(tilt_ctx* ctx) {
+    while (!ctx->waiting.empty() && !ctx->free_slots.empty()) {
+        const uint64_t id = ctx->waiting.front();
+        auto it = ctx->tickets.find(id);
+        if (it == ctx->tickets.end()) { ctx->waiting.pop_front(); continue; }
+        Ticket& t = it->second;
+        size_t off;
+        if (!ctx->pool.alloc(t.ws_bytes, &off)) break;
+        ctx->waiting.pop_front();
+        t.ws_off = off;
+        t.slot = ctx->free_slots.back();
+        ctx->free_slots.pop_back();
+        cudaStream_t st = ctx->streams[ctx->next_stream++ & 3];
+        int rc = prepare(ctx, t, st);
+        if (rc) return rc;
+        t.req.host_copy.clear();
+        t.req.host_copy.shrink_to_fit();
+        int* ord = reinterpret_cast<int*>(ctx->pool_base + t.ws_off + t.lay.order);
+        const int slot = t.slot;
+        CUDA_TRY(cudaMemcpyAsync(ord, &slot, sizeof(int), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(launch_solver(ctx->probs_dev, ord, 1, t.lay.minb, t.lay.smem, st));
+        ctx->launches++;
+    }
+    return TILT_OK;
+}
+
+void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
+    memset(out, 0, sizeof *out);
+    out->status = r.status;
+    out->p = r.p;
+    for (int k = 0; k < 8; ++k) out->tau[k] = r.tau[k];
+    out->objective = r.objective;
+    out->lambda = r.lambda;
+    out->rank_A = r.rank_A;
+    out->outer_iters = r.outer_iters;
+    out->inner_iters = r.inner_iters;
+    out->svd_sweeps = r.svd_sweeps;
+    out->svd_warm = r.svd_warm;
+    out->oob_pixels = r.oob_pixels;
+    out->kkt_residual = r.kkt_residual;
+    out->latency_ms = (float)(t.t_done - t.t_submit);
+}
+
+// Copy a device plane (long-side-contiguous) to a host m x n row-major array.
+int fetch_plane(tilt_ctx* ctx, const float* dev, int m, int n, float* host) {
+    const Dims d = make_dims(m, n, 0);
+    std::vector<float> tmp((size_t)d.S);
+    CUDA_TRY(cudaMemcpyAsync(tmp.data(), dev, sizeof(float) * d.S, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));
+    if (d.colmajor) {
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < m; ++i) host[(size_t)i * n + j] = tmp[(size_t)j * m + i];
+    } else {
+        memcpy(host, tmp.data(), sizeof(float) * d.S);
+    }
+    return TILT_OK;
+}
+
+int ensure_scratch(tilt_ctx* ctx, size_t bytes) {
+    if (ctx->scratch_bytes >= bytes) return TILT_OK;
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    if (ctx->scratch) {
+        CUDA_TRY(cudaStreamSynchronize(ctx->streams[0]));
+        CUDA_TRY(cudaFree(ctx->scratch));
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    CUDA_TRY(cudaMalloc(&ctx->scratch, bytes));
+    ctx->scratch_bytes = bytes;
+    return TILT_OK;
+}
+
+int run_step(tilt_ctx* ctx) {
+    ctx->launches++;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(ctx->streams[0]));
+    return TILT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tilt_default_params(tilt_params* p) {
+    if (!p) return;
+    p->lambda = -1.0;
+    p->eps1 = 1e-6;
+    p->eps2 = 0.1;
+    p->rho0 = 1.5;
+    p->mu0 = -1.0;
+    p->mu_max = 1e10;
+    p->eps_svd = 0.05;
+    p->max_inner = 500;
+    p->max_outer = 10;
+    p->outer_tol = 1e-2;
+}
+
+const char* tilt_last_error(tilt_ctx*) { return g_err.c_str(); }
+
+uint64_t tilt_kernel_launches(tilt_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
+    if (!cfg || !out) return fail(TILT_E_INVAL, "null argument");
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(TILT_E_INVAL, "device %d of %d", cfg->device, ndev);
+    CUDA_TRY(cudaSetDevice(cfg->device));
+    tilt_ctx* ctx = new tilt_ctx();
+    ctx->device = cfg->device;
+    ctx->max_live = cfg->max_live > 0 ? cfg->max_live : 65536;
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device));
+    ctx->max_smem = (size_t)optin - 2048;    // static shared memory of the solver kernel
+    CUDA_TRY(configure_kernels(ctx->max_smem));
+    for (auto& s : ctx->streams) CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    size_t freeb = 0, totalb = 0;
+    CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
+    size_t budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : freeb / 4;
+    budget = std::min<size_t>(budget, freeb > (size_t(1) << 30) ? freeb - (size_t(1) << 30) : freeb / 2);
+    budget &= ~(ALIGN - 1);
+    CUDA_TRY(cudaMalloc(&ctx->pool_base, budget));
+    ctx->pool.init(budget);
+    const size_t ns = (size_t)ctx->max_live;
+    CUDA_TRY(cudaHostAlloc(&ctx->probs, ns * sizeof(Problem), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostAlloc(&ctx->res, ns * sizeof(Result), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostAlloc(&ctx->done, ns * sizeof(int), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostAlloc(&ctx->step_out, sizeof(StepOut), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->probs_dev, ctx->probs, 0));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->res_dev, ctx->res, 0));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->done_dev, ctx->done, 0));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->step_out_dev, ctx->step_out, 0));
+    memset(ctx->done, 0, ns * sizeof(int));
+    ctx->free_slots.reserve(ns);
+    for (int s = (int)ns - 1; s >= 0; --s) ctx->free_slots.push_back(s);
+    *out = ctx;
+    return TILT_OK;
+}
+
+int tilt_submit(tilt_ctx* ctx, const float* img, int H, int W, size_t ld_elems, int is_device_ptr, int m, int n,
+                const double* tau0, tilt_transform type, const tilt_params* params, uint64_t* ticket_out) {
+    if (!ctx || !tau0 || !ticket_out) return fail(TILT_E_INVAL, "null argument");
+    int rc = validate(H, W, ld_elems, m, n, (int)type, img);
+    if (rc) return rc;
+    Ticket t;
+    t.req.img = img;
+    t.req.H = H;
+    t.req.W = W;
+    t.req.ld = ld_elems;
+    t.req.is_dev = is_device_ptr ? 1 : 0;
+    t.req.m = m;
+    t.req.n = n;
+    t.req.p = (int)type;
+    for (int k = 0; k < 8; ++k) t.req.tau0[k] = k < (int)type ? tau0[k] : 0.0;
+    for (int k = 0; k < (int)type; ++k)
+        if (!std::isfinite(tau0[k])) return fail(TILT_E_INVAL, "non-finite tau0");
+    t.req.prm = to_params(params);
+    if (!params_ok(t.req.prm)) return fail(TILT_E_INVAL, "parameters out of range");
+    t.lay = plan(ctx, m, n, (int)type, H, W, !is_device_ptr);
+    t.ws_bytes = t.lay.total;
+    if (t.ws_bytes > ctx->pool.size())
+        return fail(TILT_E_NOMEM, "problem needs %zu bytes, budget is %zu", t.ws_bytes, ctx->pool.size());
+    if ((int)ctx->tickets.size() >= ctx->max_live * 4) return fail(TILT_E_BUSY, "too many outstanding tickets");
+    t.m = m;
+    t.n = n;
+    t.p = (int)type;
+    t.t_submit = now_ms();
+    const uint64_t id = ctx->next_ticket++;
+    size_t off;
+    const bool fits = ctx->waiting.empty() && !ctx->free_slots.empty() && ctx->pool.alloc(t.ws_bytes, &off);
+    if (!fits) {
+        if (!is_device_ptr) {   // keep a private copy: the caller may reuse img at once
+            t.req.host_copy.resize((size_t)H * W);
+            for (int y = 0; y < H; ++y) memcpy(&t.req.host_copy[(size_t)y * W], img + (size_t)y * ld_elems, sizeof(float) * W);
+        }
+        ctx->tickets.emplace(id, std::move(t));
+        ctx->waiting.push_back(id);
+        *ticket_out = id;
+        return TILT_OK;
+    }
+    t.ws_off = off;
+    t.slot = ctx->free_slots.back();
+    ctx->free_slots.pop_back();
+    cudaStream_t st = ctx->streams[ctx->next_stream++ & 3];
+    auto& tk = ctx->tickets.emplace(id, std::move(t)).first->second;
+    rc = prepare(ctx, tk, st);
+    if (rc) { release_ticket(ctx, id); return rc; }
+    int* ord = reinterpret_cast<int*>(ctx->pool_base + tk.ws_off + tk.lay.order);
+    const int slot = tk.slot;
+    CUDA_TRY(cudaMemcpyAsync(ord, &slot, sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(launch_solver(ctx->probs_dev, ord, 1, tk.lay.minb, tk.lay.smem, st));
+    ctx->launches++;
+    *ticket_out = id;
+    return TILT_OK;
+}
+
+int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int is_device_ptr, const tilt_params* params,
+                      uint64_t* tickets_out) {
+    if (!ctx || count < 0 || (count && (!probs || !tickets_out))) return fail(TILT_E_INVAL, "bad arguments");
+    if (count == 0) return TILT_OK;
+    const Params prm = to_params(params);
+    if (!params_ok(prm)) return fail(TILT_E_INVAL, "parameters out of range");
+    if ((int)ctx->free_slots.size() < count) return fail(TILT_E_BUSY, "%d free slots, %d problems", (int)ctx->free_slots.size(), count);
+    std::vector<Ticket> ts((size_t)count);
+    size_t total = 0;
+    for (int q = 0; q < count; ++q) {
+        const tilt_problem& pb = probs[q];
+        int rc = validate(pb.H, pb.W, pb.ld_elems, pb.m, pb.n, pb.type, pb.img);
+        if (rc) return fail(rc, "problem %d: %s", q, g_err.c_str());
+        Ticket& t = ts[q];
+        t.req.img = pb.img;
+        t.req.H = pb.H;
+        t.req.W = pb.W;
+        t.req.ld = pb.ld_elems;
+        t.req.is_dev = is_device_ptr ? 1 : 0;
+        t.req.m = pb.m;
+        t.req.n = pb.n;
+        t.req.p = pb.type;
+        for (int k = 0; k < 8; ++k) t.req.tau0[k] = k < pb.type ? pb.tau0[k] : 0.0;
+        t.req.prm = prm;
+        t.lay = plan(ctx, pb.m, pb.n, pb.type, pb.H, pb.W, !is_device_ptr);
+        t.ws_bytes = t.lay.total;
+        t.m = pb.m;
+        t.n = pb.n;
+        t.p = pb.type;
+        if (t.ws_bytes > ctx->pool.size()) return fail(TILT_E_NOMEM, "problem %d needs %zu bytes", q, t.ws_bytes);
+        total += align_up(t.ws_bytes);
+    }
+    // grouped launches: one per occupancy class, largest problems first
+    std::vector<int> idx(count);
+    for (int q = 0; q < count; ++q) idx[q] = q;
+    std::vector<int> klass(count);
+    for (int q = 0; q < count; ++q) klass[q] = ts[q].lay.smem_svd ? (ts[q].lay.minb == 2 ? 0 : 1) : 2;
+    auto cls = [&](int q) { return klass[q]; };
+    auto cost = [&](int q) {
+        const Dims d = make_dims(ts[q].m, ts[q].n, ts[q].p);
+        return (double)d.R * d.C * d.C;
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        if (cls(a) != cls(b)) return cls(a) < cls(b);
+        return cost(a) > cost(b);
+    });
+    const size_t order_bytes = align_up(sizeof(int) * count);
+    size_t boff;
+    if (!ctx->pool.alloc(order_bytes, &boff)) return fail(TILT_E_BUSY, "device memory for the batch order is in use");
+    std::vector<size_t> offs(count);
+    int got = 0;
+    for (; got < count; ++got) {
+        if (!ctx->pool.alloc(ts[got].ws_bytes, &offs[got])) break;
+    }
+    if (got < count) {
+        for (int q = 0; q < got; ++q) ctx->pool.release(offs[q], ts[q].ws_bytes);
+        ctx->pool.release(boff, order_bytes);
+        return fail(TILT_E_BUSY, "batch needs %zu bytes; %zu of %zu in use", total, ctx->pool.used(), ctx->pool.size());
+    }
+    const int bid = ctx->next_batch++;
+    ctx->batches[bid] = Batch{boff, order_bytes, count};
+    const double t0 = now_ms();
+    std::vector<uint64_t> ids(count);
+    std::vector<int> order(count);
+    for (int q = 0; q < count; ++q) {
+        Ticket& t = ts[q];
+        t.ws_off = offs[q];
+        t.slot = ctx->free_slots.back();
+        ctx->free_slots.pop_back();
+        t.batch = bid;
+        t.t_submit = t0;
+        ids[q] = ctx->next_ticket++;
+    }
+    cudaStream_t st[3] = {ctx->streams[0], ctx->streams[1], ctx->streams[2]};
+    for (int q = 0; q < count; ++q) {
+        Ticket& t = ctx->tickets.emplace(ids[q], std::move(ts[q])).first->second;
+        int rc = prepare(ctx, t, st[cls(q)]);
+        if (rc) return rc;
+        order[q] = t.slot;
+        tickets_out[q] = ids[q];
+    }
+    std::vector<int> ord_slots(count);
+    for (int q = 0; q < count; ++q) ord_slots[q] = order[idx[q]];
+    int* ord_dev = reinterpret_cast<int*>(ctx->pool_base + boff);
+    // the order array is copied once (pageable source: staged before the call returns)
+    CUDA_TRY(cudaMemcpyAsync(ord_dev, ord_slots.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st[0]));
+    CUDA_TRY(cudaStreamSynchronize(st[0]));
+    int start = 0;
+    while (start < count) {
+        const int c = cls(idx[start]);
+        int end = start;
+        size_t smem = 0;
+        while (end < count && cls(idx[end]) == c) {
+            smem = std::max(smem, ctx->tickets[ids[idx[end]]].lay.smem);
+            ++end;
+        }
+        const int minb = (c == 0) ? 2 : 1;
+        CUDA_TRY(launch_solver(ctx->probs_dev, ord_dev + start, end - start, minb, smem, st[c]));
+        ctx->launches++;
+        start = end;
+    }
+    return TILT_OK;
+}
+
+int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, float* E_out) {
+    if (!ctx) return fail(TILT_E_INVAL, "null context");
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(TILT_E_NOTFOUND, "ticket %llu", (unsigned long long)ticket);
+    Ticket& t = it->second;
+    if (t.slot < 0) {
+        int rc = admit_waiting(ctx);
+        if (rc) return rc;
+        return TILT_PENDING;
+    }
+    if (!reinterpret_cast<volatile int*>(ctx->done)[t.slot]) {
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) return fail(TILT_E_CUDA, "CUDA error while waiting: %s", cudaGetErrorString(e));
+        return TILT_PENDING;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (t.t_done == 0) t.t_done = now_ms();
+    const Result r = ctx->res[t.slot];
+    if (A_out) {
+        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.A, t.m, t.n, A_out);
+        if (rc) return rc;
+    }
+    if (E_out) {
+        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.E, t.m, t.n, E_out);
+        if (rc) return rc;
+    }
+    if (out) fill_result(r, t, out);
+    release_ticket(ctx, ticket);
+    return admit_waiting(ctx);
+}
+
+int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, float* A_out, float* E_out) {
+    const double t_end = now_ms() + (timeout_ms < 0 ? 60000.0 : (double)timeout_ms);
+    for (;;) {
+        int rc = tilt_poll(ctx, ticket, out, A_out, E_out);
+        if (rc != TILT_PENDING) return rc;
+        if (now_ms() > t_end) return fail(TILT_E_TIMEOUT, "ticket %llu still running", (unsigned long long)ticket);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+int tilt_destroy(tilt_ctx* ctx) {
+    if (!ctx) return TILT_OK;
+    cudaSetDevice(ctx->device);
+    const double t_end = now_ms() + 120000.0;
+    for (;;) {
+        bool busy = false;
+        for (auto s : ctx->streams) busy = busy || cudaStreamQuery(s) == cudaErrorNotReady;
+        busy = busy || cudaStreamQuery(ctx->copy_stream) == cudaErrorNotReady;
+        if (!busy) break;
+        if (now_ms() > t_end) return fail(TILT_E_TIMEOUT, "work still running after 120 s; context leaked");
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+    for (auto s : ctx->streams) cudaStreamDestroy(s);
+    cudaStreamDestroy(ctx->copy_stream);
+    cudaFree(ctx->pool_base);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    cudaFreeHost(ctx->probs);
+    cudaFreeHost(ctx->res);
+    cudaFreeHost(ctx->done);
+    cudaFreeHost(ctx->step_out);
+    delete ctx;
+    return TILT_OK;
+}
+
+// ------------------------------------------------------------------------------ step entry points
+int tilt_warp_jacobian(tilt_ctx* ctx, const float* img_dev, int H, int W, size_t ld, int m, int n, const double* tau,
+                       tilt_transform type, float* Dhat_dev, float* J_dev, double* norm_out, int* oob_out) {
+    if (!ctx || !tau || !Dhat_dev || !J_dev) return fail(TILT_E_INVAL, "null argument");
+    int rc = validate(H, W, ld, m, n, (int)type, img_dev);
+    if (rc) return rc;
+    WarpArgs a{};
+    a.img = img_dev;
+    a.ld = (long long)ld;
+    a.H = H; a.W = W; a.m = m; a.n = n; a.ttype = (int)type;
+    for (int k = 0; k < PMAX; ++k) a.tau[k] = k < (int)type ? tau[k] : 0.0;
+    a.Dhat = Dhat_dev;
+    a.J = J_dev;
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_warp_step(a, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    if (norm_out) *norm_out = ctx->step_out->norm;
+    if (oob_out) *oob_out = ctx->step_out->oob;
+    return TILT_OK;
+}
+
+int tilt_gram(tilt_ctx* ctx, const float* J_dev, int m, int n, const double* tau, tilt_transform type, double* Q_out,
+              double* G_out, double* Ginv_out) {
+    if (!ctx || !tau || !J_dev) return fail(TILT_E_INVAL, "null argument");
+    if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "window %d x %d", m, n);
+    if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "bad type");
+    int rc = ensure_scratch(ctx, sizeof(float) * (size_t)m * n);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(ctx->scratch, 0, sizeof(float) * (size_t)m * n, ctx->streams[0]));
+    GramArgs a{};
+    a.J = J_dev;
+    a.Dhat = reinterpret_cast<const float*>(ctx->scratch);
+    a.m = m; a.n = n; a.ttype = (int)type;
+    for (int k = 0; k < PMAX; ++k) a.tau[k] = k < (int)type ? tau[k] : 0.0;
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_gram_step(a, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    const int p = (int)type;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < p; ++c)
+            if (Q_out) Q_out[r * p + c] = ctx->step_out->Q[r * PMAX + c];
+    for (int r = 0; r < p; ++r)
+        for (int c = 0; c < p; ++c) {
+            if (G_out) G_out[r * p + c] = ctx->step_out->G[r * PMAX + c];
+            if (Ginv_out) Ginv_out[r * p + c] = ctx->step_out->Gi[r * PMAX + c];
+        }
+    if (ctx->step_out->status) return fail(TILT_E_INVAL, "J^T J + Q^T Q is singular");
+    return TILT_OK;
+}
+
+int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* A_dev, float* sigma_out, int* sweeps_out) {
+    if (!ctx || !M_dev || !A_dev) return fail(TILT_E_INVAL, "null argument");
+    if (m < 1 || n < 1 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "matrix %d x %d", m, n);
+    if (!(eps >= 0.f)) return fail(TILT_E_INVAL, "eps must be >= 0");
+    const Dims d = make_dims(m, n, 0);
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
+    SvtArgs a{};
+    a.M = M_dev;
+    a.A = A_dev;
+    a.m = m; a.n = n; a.eps = eps;
+    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+    const size_t need = sizeof(float) * (a.smem_svd ? 0 : (2 * nb + nv)) + sizeof(float) * MAX_SIDE;
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    float* s = reinterpret_cast<float*>(ctx->scratch);
+    a.sigma = s;
+    if (!a.smem_svd) {
+        a.Bg = s + MAX_SIDE;
+        a.Vg = a.Bg + nb;
+        a.Tg = a.Vg + nv;
+    }
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_svt_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    if (sigma_out) CUDA_TRY(cudaMemcpy(sigma_out, a.sigma, sizeof(float) * d.C, cudaMemcpyDeviceToHost));
+    if (sweeps_out) *sweeps_out = ctx->step_out->sweeps;
+    return TILT_OK;
+}
+
+int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, int n, const double* tau, tilt_transform type,
+               const tilt_params* params, double mu0, float* A_dev, float* E_dev, float* Y_dev, int* iters_out,
+               double* dtau_out, double* c1_out, double* c2_out, double* mu_out) {
+    if (!ctx || !Dhat_dev || !J_dev || !tau || !A_dev || !E_dev || !Y_dev) return fail(TILT_E_INVAL, "null argument");
+    if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "window %d x %d", m, n);
+    if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "bad type");
+    InnerArgs a{};
+    a.prm = to_params(params);
+    if (!params_ok(a.prm)) return fail(TILT_E_INVAL, "parameters out of range");
+    const Dims d = make_dims(m, n, (int)type);
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
+    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+    const size_t need = sizeof(float) * (2 * (size_t)d.S + (a.smem_svd ? 0 : (2 * nb + nv)));
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    float* s = reinterpret_cast<float*>(ctx->scratch);
+    a.P = s;
+    a.Mp = s + d.S;
+    if (!a.smem_svd) {
+        a.Bg = a.Mp + d.S;
+        a.Vg = a.Bg + nb;
+        a.Tg = a.Vg + nv;
+    }
+    a.Dhat = Dhat_dev;
+    a.J = J_dev;
+    a.A = A_dev;
+    a.E = E_dev;
+    a.Y = Y_dev;
+    a.m = m; a.n = n; a.ttype = (int)type;
+    for (int k = 0; k < PMAX; ++k) a.tau[k] = k < (int)type ? tau[k] : 0.0;
+    a.mu0 = mu0;
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_inner_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    const StepOut& o = *ctx->step_out;
+    if (o.status == -2) return fail(TILT_E_INVAL, "J^T J + Q^T Q is singular");
+    if (iters_out) *iters_out = o.iters;
+    if (dtau_out)
+        for (int k = 0; k < (int)type; ++k) dtau_out[k] = o.dtau[k];
+    if (c1_out) *c1_out = o.c1;
+    if (c2_out) *c2_out = o.c2;
+    if (mu_out) *mu_out = o.mu;
+    return TILT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,610 @@
+// Device code of the TILT-by-LADMAP solver: every function here is executed by all
+// threads of one CTA, which owns one problem (window) for the duration of the call.
+//
+// Storage of an m x n window ("long-side contiguous"): R = max(m, n), C = min(m, n);
+// element (i, j) lives at X(r, c) = c*R + r with (r, c) = (i, j) when m >= n and
+// (r, c) = (j, i) otherwise.  The one-sided Jacobi SVD then works on the C contiguous
+// columns of length R of the matrix X (X = M when m >= n, X = M^T otherwise; the singular
+// value thresholding of Eq. A_1 commutes with transposition).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace tilt {
+
+constexpr int NT = 512;          // threads per CTA
+constexpr int NW = NT / 32;      // warps per CTA
+constexpr int PMAX = 8;          // largest transform (projective)
+constexpr int MAX_SIDE = 512;
+
+// ------------------------------------------------------------------------------ parameters
+struct Params {
+    double lam, eps1, eps2, rho0, mu0, mu_max, eps_svd, outer_tol;
+    int max_inner, max_outer;
+};
+
+// Per-problem result record (written once, at the end of the solve).
+struct Result {
+    int status;
+    int p;
+    double tau[8];
+    double objective;
+    double lambda;
+    int rank_A, outer_iters, inner_iters, svd_sweeps, svd_warm, oob_pixels;
+    double kkt_residual;
+    // per-phase clock counters (SM cycles), for the time split of the fused solver
+    unsigned long long cyc_warp, cyc_svd, cyc_recon, cyc_elem, cyc_other;
+};
+
+// Planes of one problem in device global memory (long-side-contiguous layout).
+struct Planes {
+    float* Dhat;   // S
+    float* J;      // p * S
+    float* A;      // S
+    float* E;      // S
+    float* Y;      // S   (the scaled multiplier Y~ = W^T Y of Sec. 4.3)
+    float* P;      // S   (W^T W (A + E - D_hat), carried between iterations)
+    float* Mp;     // S   (previous M, for the warm-start gate)
+    float* Bg;     // ldb * Cp  (SVD work, global mode only)
+    float* Vg;     // ldv * Cp
+    float* Tg;     // ldb * Cp
+};
+
+// One problem as the solver kernel sees it.
+struct Problem {
+    const float* img;
+    long long ld;
+    int H, W;
+    int m, n, p, ttype;
+    double tau[8];
+    Params prm;
+    Planes pl;
+    int smem_svd;          // 1: B, V, T live in shared memory
+    Result* res;           // host-mapped result record
+    volatile int* done;    // host-mapped completion flag
+};
+
+struct Dims {
+    int m, n, R, C, S, p;
+    bool colmajor;         // m >= n
+    int ldb, ldv, Cp;      // SVD buffer geometry (Cp = C rounded up to 4)
+};
+
+__host__ __device__ inline Dims make_dims(int m, int n, int p) {
+    Dims d;
+    d.m = m; d.n = n; d.p = p;
+    d.colmajor = (m >= n);
+    d.R = d.colmajor ? m : n;
+    d.C = d.colmajor ? n : m;
+    d.S = m * n;
+    d.ldb = (d.R + 3) & ~3;
+    d.Cp = (d.C + 3) & ~3;
+    d.ldv = d.Cp;
+    return d;
+}
+
+// Shared-memory bytes of the SVD buffers B, V, T.
+__host__ __device__ inline size_t svd_smem_bytes(const Dims& d) {
+    return sizeof(float) * ((size_t)2 * d.ldb * d.Cp + (size_t)d.ldv * d.Cp);
+}
+
+// ------------------------------------------------------------------------------ CTA scratch
+// Small per-CTA scalars kept in shared memory.
+struct Scratch {
+    double red[16 * NW];       // block-reduction staging
+    double G[PMAX * PMAX];     // J^T J + Q^T Q
+    double Gi[PMAX * PMAX];    // its inverse
+    double Q[3 * PMAX];
+    double jd[PMAX];           // J^T D_hat
+    double ja[PMAX];           // J^T A
+    double je[PMAX];           // J^T E
+    double cvec[PMAX];         // coefficients c = G^-1 J^T (.) of the current W^T W product
+    double tau[PMAX];
+    double dtau[PMAX];
+    double scal[16];           // broadcast scalars
+    int iscal[8];
+    int flag[2];
+};
+
+// Dynamic shared memory layout: [Scratch][sigma: C floats][w: C floats][kept: C ints][B|V|T]
+struct SmemLayout {
+    Scratch* sc;
+    float* sigma;
+    float* w;
+    int* kept;
+    float* svd;
+};
+
+__host__ __device__ inline size_t smem_head_bytes() {
+    size_t b = sizeof(Scratch);
+    b += sizeof(float) * MAX_SIDE * 2 + sizeof(int) * MAX_SIDE;
+    return (b + 255) & ~(size_t)255;
+}
+
+__device__ inline SmemLayout carve_smem(unsigned char* base) {
+    SmemLayout L;
+    L.sc = reinterpret_cast<Scratch*>(base);
+    unsigned char* p = base + sizeof(Scratch);
+    L.sigma = reinterpret_cast<float*>(p);
+    L.w = L.sigma + MAX_SIDE;
+    L.kept = reinterpret_cast<int*>(L.w + MAX_SIDE);
+    L.svd = reinterpret_cast<float*>(base + smem_head_bytes());
+    return L;
+}
+
+// ------------------------------------------------------------------------------ reductions
+// Sum K doubles over the CTA; every thread gets the totals.  Fixed order -> deterministic.
+template <int K>
+__device__ inline void block_sum(double (&v)[K], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * NW + warp] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += red[k * NW + w];
+        v[k] = s;
+    }
+    __syncthreads();
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Window pixel of storage index e.
+__device__ inline void pixel_of(const Dims& d, int e, int& i, int& j) {
+    int r = e % d.R, c = e / d.R;
+    if (d.colmajor) { i = r; j = c; } else { i = c; j = r; }
+}
+
+// ------------------------------------------------------------------------------ transforms
+// tau(u, v) -> (x, y) in FP64 with the operation order ((t0 u + t1 v) + t2), every
+// operation rounded to nearest, so that the pixel-cell decision of the bilinear warp is
+// bit-identical to a plain FP64 evaluation.
+struct MapPt {
+    double x, y, den;
+};
+
+__device__ inline MapPt map_point(const double* t, int ttype, double u, double v) {
+    MapPt q;
+    double nx = __dadd_rn(__dadd_rn(__dmul_rn(t[0], u), __dmul_rn(t[1], v)), t[2]);
+    double ny = __dadd_rn(__dadd_rn(__dmul_rn(t[3], u), __dmul_rn(t[4], v)), t[5]);
+    if (ttype == 8) {
+        double den = __dadd_rn(__dadd_rn(__dmul_rn(t[6], u), __dmul_rn(t[7], v)), 1.0);
+        q.x = __ddiv_rn(nx, den);
+        q.y = __ddiv_rn(ny, den);
+        q.den = den;
+    } else {
+        q.x = nx;
+        q.y = ny;
+        q.den = 1.0;
+    }
+    return q;
+}
+
+// d x / d tau and d y / d tau at (u, v) (FP64).
+__device__ inline void map_derivs(const MapPt& q, int ttype, double u, double v, double* dx, double* dy) {
+    if (ttype == 8) {
+        double iu = u / q.den, iv = v / q.den, i1 = 1.0 / q.den;
+        dx[0] = iu; dx[1] = iv; dx[2] = i1; dx[3] = 0; dx[4] = 0; dx[5] = 0; dx[6] = -q.x * iu; dx[7] = -q.x * iv;
+        dy[0] = 0; dy[1] = 0; dy[2] = 0; dy[3] = iu; dy[4] = iv; dy[5] = i1; dy[6] = -q.y * iu; dy[7] = -q.y * iv;
+    } else {
+        dx[0] = u; dx[1] = v; dx[2] = 1; dx[3] = 0; dx[4] = 0; dx[5] = 0;
+        dy[0] = 0; dy[1] = 0; dy[2] = 0; dy[3] = u; dy[4] = v; dy[5] = 1;
+    }
+}
+
+// ------------------------------------------------------------------------------ K1
+// Algorithm 1, Step 1: warp + normalise + Jacobian of the normalised warp.
+// Writes D_hat and J; returns ||D o tau||_F (scal[0]) and the clamped-sample count (iscal[0]).
+static __device__ void k1_warp_jacobian(const float* __restrict__ img, long long ld, int H, int W,
+                                 const Dims& d, int ttype, const double* tau,
+                                 float* __restrict__ Dhat, float* __restrict__ J, Scratch* sc) {
+    const int p = d.p, S = d.S;
+    const double hm = 0.5 * (d.m - 1), hn = 0.5 * (d.n - 1);
+    const double Wm1 = (double)(W - 1), Hm1 = (double)(H - 1);
+    double acc[2 + PMAX];
+#pragma unroll
+    for (int k = 0; k < 2 + PMAX; ++k) acc[k] = 0.0;
+    for (int e = threadIdx.x; e < S; e += NT) {
+        int i, j;
+        pixel_of(d, e, i, j);
+        const double u = (double)j - hn, v = (double)i - hm;
+        MapPt q = map_point(tau, ttype, u, v);
+        const bool inx = (q.x >= 0.0) && (q.x <= Wm1);
+        const bool iny = (q.y >= 0.0) && (q.y <= Hm1);
+        const double xc = fmin(fmax(q.x, 0.0), Wm1);
+        const double yc = fmin(fmax(q.y, 0.0), Hm1);
+        const double x0 = fmin(floor(xc), (double)(W - 2));
+        const double y0 = fmin(floor(yc), (double)(H - 2));
+        const float fx = (float)(xc - x0), fy = (float)(yc - y0);
+        const long long xi = (long long)x0, yi = (long long)y0;
+        const float* row0 = img + yi * ld + xi;
+        const float I00 = __ldg(row0), I01 = __ldg(row0 + 1);
+        const float I10 = __ldg(row0 + ld), I11 = __ldg(row0 + ld + 1);
+        const float val = (1.f - fy) * ((1.f - fx) * I00 + fx * I01) + fy * ((1.f - fx) * I10 + fx * I11);
+        const float gx = inx ? ((1.f - fy) * (I01 - I00) + fy * (I11 - I10)) : 0.f;
+        const float gy = iny ? ((1.f - fx) * (I10 - I00) + fx * (I11 - I01)) : 0.f;
+        double dx[PMAX], dy[PMAX];
+        map_derivs(q, ttype, u, v, dx, dy);
+        Dhat[e] = val;
+        acc[0] += (double)val * (double)val;
+        acc[1] += (inx && iny) ? 0.0 : 1.0;
+#pragma unroll
+        for (int k = 0; k < PMAX; ++k) {
+            if (k < p) {
+                const float jr = gx * (float)dx[k] + gy * (float)dy[k];
+                J[(size_t)k * S + e] = jr;
+                acc[2 + k] += (double)val * (double)jr;
+            }
+        }
+    }
+    block_sum<2 + PMAX>(acc, sc->red);
+    const double s = sqrt(acc[0]);
+    if (threadIdx.x == 0) {
+        sc->scal[0] = s;
+        sc->iscal[0] = (int)acc[1];
+    }
+    const float inv = (s > 0.0) ? (float)(1.0 / s) : 0.f;
+    float a[PMAX];
+#pragma unroll
+    for (int k = 0; k < PMAX; ++k) a[k] = (s > 0.0 && k < p) ? (float)(acc[2 + k] / (s * s)) : 0.f;
+    for (int e = threadIdx.x; e < S; e += NT) {
+        const float D = Dhat[e];
+        Dhat[e] = D * inv;
+#pragma unroll
+        for (int k = 0; k < PMAX; ++k) {
+            if (k < p) {
+                float* jp = J + (size_t)k * S + e;
+                *jp = (*jp - D * a[k]) * inv;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ K5 (Gram)
+// Q rows (Sec. 4.3): derivatives of the centroid of the mapped window corners and of the
+// signed area of the mapped quadrilateral (area row / ((m-1)(n-1))).  Thread 0 only.
+__device__ inline void constraint_rows(const double* tau, int ttype, int m, int n, int p, double* Q) {
+    const double a = 0.5 * (n - 1), b = 0.5 * (m - 1);
+    const double cu[4] = {-a, a, a, -a}, cv[4] = {-b, -b, b, b};
+    double x[4], y[4], dx[4][PMAX], dy[4][PMAX];
+    for (int c = 0; c < 4; ++c) {
+        MapPt q = map_point(tau, ttype, cu[c], cv[c]);
+        x[c] = q.x; y[c] = q.y;
+        map_derivs(q, ttype, cu[c], cv[c], dx[c], dy[c]);
+    }
+    const double norm = 1.0 / ((double)(m - 1) * (double)(n - 1));
+    for (int k = 0; k < p; ++k) {
+        double qx = 0, qy = 0, da = 0;
+        for (int c = 0; c < 4; ++c) {
+            const int c1 = (c + 1) & 3;
+            qx += dx[c][k];
+            qy += dy[c][k];
+            da += dx[c][k] * y[c1] + x[c] * dy[c1][k] - dx[c1][k] * y[c] - x[c1] * dy[c][k];
+        }
+        Q[0 * PMAX + k] = 0.25 * qx;
+        Q[1 * PMAX + k] = 0.25 * qy;
+        Q[2 * PMAX + k] = 0.5 * da * norm;
+    }
+}
+
+// Gauss-Jordan inverse with partial pivoting of a p x p FP64 matrix (row stride PMAX).
+// Returns false when singular.  Thread 0 only.
+__device__ inline bool invert_pp(const double* G, double* Gi, int p) {
+    double a[PMAX][2 * PMAX];
+    for (int r = 0; r < p; ++r)
+        for (int c = 0; c < 2 * p; ++c) a[r][c] = (c < p) ? G[r * PMAX + c] : (c - p == r ? 1.0 : 0.0);
+    double scale = 0.0;
+    for (int r = 0; r < p; ++r) scale = fmax(scale, fabs(G[r * PMAX + r]));
+    for (int col = 0; col < p; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < p; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (!(fabs(a[piv][col]) > 1e-300) || !(fabs(a[piv][col]) > 1e-14 * scale)) return false;
+        if (piv != col)
+            for (int c = 0; c < 2 * p; ++c) { double t = a[col][c]; a[col][c] = a[piv][c]; a[piv][c] = t; }
+        const double inv = 1.0 / a[col][col];
+        for (int c = 0; c < 2 * p; ++c) a[col][c] *= inv;
+        for (int r = 0; r < p; ++r) {
+            if (r == col) continue;
+            const double f = a[r][col];
+            if (f != 0.0)
+                for (int c = 0; c < 2 * p; ++c) a[r][c] -= f * a[col][c];
+        }
+    }
+    for (int r = 0; r < p; ++r)
+        for (int c = 0; c < p; ++c) Gi[r * PMAX + c] = a[r][p + c];
+    return true;
+}
+
+// G = J^T J + Q^T Q, G^-1, J^T D_hat and ||D_hat||^2, d0 = ||W^T W D_hat||_F (FP64).
+// Returns false when G is singular.  Results in sc->G, sc->Gi, sc->Q, sc->jd, scal[1] (d0).
+static __device__ bool k5_gram(const Dims& d, int ttype, const double* tau, const float* __restrict__ Dhat,
+                        const float* __restrict__ J, Scratch* sc) {
+    const int p = d.p, S = d.S;
+    // pairs (a <= b) then J^T D_hat then ||D_hat||^2
+    constexpr int NPAIR = PMAX * (PMAX + 1) / 2;
+    double acc[NPAIR + PMAX + 1];
+#pragma unroll
+    for (int k = 0; k < NPAIR + PMAX + 1; ++k) acc[k] = 0.0;
+    for (int e = threadIdx.x; e < S; e += NT) {
+        double jv[PMAX];
+#pragma unroll
+        for (int k = 0; k < PMAX; ++k) jv[k] = (k < p) ? (double)J[(size_t)k * S + e] : 0.0;
+        const double dh = (double)Dhat[e];
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < PMAX; ++a)
+#pragma unroll
+            for (int b = a; b < PMAX; ++b) acc[q++] += jv[a] * jv[b];
+#pragma unroll
+        for (int a = 0; a < PMAX; ++a) acc[NPAIR + a] += jv[a] * dh;
+        acc[NPAIR + PMAX] += dh * dh;
+    }
+    block_sum<NPAIR + PMAX + 1>(acc, sc->red);
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        constraint_rows(tau, ttype, d.m, d.n, p, sc->Q);
+        int q = 0;
+        for (int a = 0; a < PMAX; ++a)
+            for (int b = a; b < PMAX; ++b) {
+                double g = acc[q++];
+                if (a < p && b < p) {
+                    for (int l = 0; l < 3; ++l) g += sc->Q[l * PMAX + a] * sc->Q[l * PMAX + b];
+                    sc->G[a * PMAX + b] = g;
+                    sc->G[b * PMAX + a] = g;
+                }
+            }
+        for (int a = 0; a < p; ++a) sc->jd[a] = acc[NPAIR + a];
+        const bool ok = invert_pp(sc->G, sc->Gi, p);
+        ok_s = ok ? 1 : 0;
+        // ||W^T W D||^2 = ||D||^2 - 2 jd^T c + c^T (J^T J) c with c = G^-1 jd
+        double c[PMAX];
+        for (int a = 0; a < p; ++a) {
+            double s = 0;
+            for (int b = 0; b < p; ++b) s += sc->Gi[a * PMAX + b] * sc->jd[b];
+            c[a] = s;
+        }
+        double q2 = acc[NPAIR + PMAX];
+        int qq = 0;
+        for (int a = 0; a < PMAX; ++a)
+            for (int b = a; b < PMAX; ++b) {
+                const double jj = acc[qq++];
+                if (a < p && b < p) q2 += (a == b ? 1.0 : 2.0) * c[a] * c[b] * jj;
+            }
+        for (int a = 0; a < p; ++a) q2 -= 2.0 * sc->jd[a] * c[a];
+        sc->scal[1] = sqrt(fmax(q2, 0.0));
+        sc->scal[2] = acc[NPAIR + PMAX];
+    }
+    __syncthreads();
+    const bool ok = ok_s != 0;
+    __syncthreads();
+    return ok;
+}
+
+// c = G^-1 v for a p-vector (thread 0 writes sc->cvec).
+__device__ inline void ginv_apply(const Scratch* sc, int p, const double* v, double* out) {
+    for (int a = 0; a < p; ++a) {
+        double s = 0;
+        for (int b = 0; b < p; ++b) s += sc->Gi[a * PMAX + b] * v[b];
+        out[a] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------ ||D_hat||_2
+// Largest singular value of the R x C matrix X (long-side-contiguous) by power iteration
+// on X^T X in FP32 with FP64 norms; xv (C) and yv (R) are shared-memory work vectors.
+static __device__ double spectral_norm(const float* __restrict__ X, const Dims& d, float* xv, float* yv, Scratch* sc) {
+    const int R = d.R, C = d.C;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = threadIdx.x; c < C; c += NT) xv[c] = rsqrtf((float)C);
+    __syncthreads();
+    double prev = 0.0, sig = 0.0;
+    int stable = 0;
+    for (int it = 0; it < 300; ++it) {
+        // y = X x
+        double ny[1] = {0.0};
+        for (int r = threadIdx.x; r < R; r += NT) {
+            float s = 0.f;
+            for (int c = 0; c < C; ++c) s += X[(size_t)c * R + r] * xv[c];
+            yv[r] = s;
+            ny[0] += (double)s * s;
+        }
+        block_sum<1>(ny, sc->red);
+        sig = sqrt(ny[0]);
+        // x = X^T y / ||X^T y||
+        double nx[1] = {0.0};
+        for (int c = warp; c < C; c += NW) {
+            float s = 0.f;
+            for (int r = lane; r < R; r += 32) s += X[(size_t)c * R + r] * yv[r];
+            s = warp_sum(s);
+            if (lane == 0) xv[c] = s;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < C; c += NT) nx[0] += (double)xv[c] * xv[c];
+        block_sum<1>(nx, sc->red);
+        const float inv = nx[0] > 0 ? (float)(1.0 / sqrt(nx[0])) : 0.f;
+        for (int c = threadIdx.x; c < C; c += NT) xv[c] *= inv;
+        __syncthreads();
+        if (fabs(sig - prev) <= 1e-7 * sig) {
+            if (++stable >= 2) break;
+        } else {
+            stable = 0;
+        }
+        prev = sig;
+    }
+    return sig;
+}
+
+// ------------------------------------------------------------------------------ K2: SVD
+// One-sided (Hestenes) Jacobi on the columns of B (R x C, column stride ldb), accumulating
+// the rotations into V (C x C, stride ldv).  Round-robin ordering: every round is a set of
+// disjoint column pairs, one pair per warp at a time, rows spread over the lanes; the
+// three dot products of a pair are reduced with warp shuffles.  A pair is rotated when
+// |b_i . b_j| > tol ||b_i|| ||b_j||; the sweeps stop when a sweep rotates nothing.
+// Returns the number of sweeps.
+static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
+                         int* flag) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Ce = C + (C & 1);
+    const int npairs = Ce / 2;
+    const int nrounds = Ce - 1;
+    int sweep = 0;
+    if (C < 2) return 0;
+    while (sweep < max_sweeps) {
+        if (threadIdx.x == 0) flag[sweep & 1] = 0;
+        __syncthreads();
+        bool rotated = false;
+        for (int round = 0; round < nrounds; ++round) {
+            for (int k = warp; k < npairs; k += NW) {
+                const int i = (k == 0) ? 0 : 1 + (k - 1 + round) % nrounds;
+                const int j = 1 + (Ce - 2 - k + round) % nrounds;
+                if (i >= C || j >= C) continue;
+                float* bi = B + (size_t)i * ldb;
+                float* bj = B + (size_t)j * ldb;
+                float a = 0.f, b = 0.f, g = 0.f;
+                for (int r = lane; r < R; r += 32) {
+                    const float x = bi[r], y = bj[r];
+                    a = fmaf(x, x, a);
+                    b = fmaf(y, y, b);
+                    g = fmaf(x, y, g);
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                g = warp_sum(g);
+                if (fabsf(g) > tol * sqrtf(a) * sqrtf(b)) {
+                    const float zeta = (b - a) / (2.f * g);
+                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                    const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
+                    const float s = c * t;
+                    for (int r = lane; r < R; r += 32) {
+                        const float x = bi[r], y = bj[r];
+                        bi[r] = c * x - s * y;
+                        bj[r] = s * x + c * y;
+                    }
+                    float* vi = V + (size_t)i * ldv;
+                    float* vj = V + (size_t)j * ldv;
+                    for (int r = lane; r < C; r += 32) {
+                        const float x = vi[r], y = vj[r];
+                        vi[r] = c * x - s * y;
+                        vj[r] = s * x + c * y;
+                    }
+                    rotated = true;
+                }
+            }
+            __syncthreads();
+        }
+        if (rotated) flag[sweep & 1] = 1;
+        __syncthreads();
+        const int any = flag[sweep & 1];
+        ++sweep;
+        if (!any) break;
+    }
+    return sweep;
+}
+
+// Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the
+// list of kept columns.  Returns (via scal) sum (sigma - eps)_+, max (sigma - eps)_+ and
+// the kept count (iscal[1]).
+static __device__ void svt_weights(const float* B, int ldb, int R, int C, float eps, float* sigma, float* w, int* kept,
+                            Scratch* sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < C; k += NW) {
+        const float* bk = B + (size_t)k * ldb;
+        float s = 0.f;
+        for (int r = lane; r < R; r += 32) s = fmaf(bk[r], bk[r], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            const float sg = sqrtf(s);
+            sigma[k] = sg;
+            w[k] = (sg > eps) ? (sg - eps) / sg : 0.f;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nk = 0;
+        double nuc = 0.0, mx = 0.0;
+        for (int k = 0; k < C; ++k) {
+            if (w[k] > 0.f) {
+                kept[nk++] = k;
+                const double sv = (double)sigma[k] - (double)eps;
+                nuc += sv;
+                mx = fmax(mx, sv);
+            }
+        }
+        sc->iscal[1] = nk;
+        sc->scal[3] = nuc;
+        sc->scal[4] = mx;
+        // numerical rank at 1e-3 of the largest kept value
+        int rk = 0;
+        for (int q = 0; q < nk; ++q)
+            if ((double)sigma[kept[q]] - (double)eps > 1e-3 * mx) ++rk;
+        sc->iscal[2] = rk;
+    }
+    __syncthreads();
+}
+
+// B = T V (R x C times C x C), 4 x 4 register tiles; T, B stride ldb (multiple of 4),
+// V stride ldv.  Works on padded sizes (ldb rows, Cp columns).
+static __device__ void gemm_TV(const float* __restrict__ T, int ldb, const float* __restrict__ V, int ldv, float* __restrict__ B,
+                        int Cp, int C) {
+    const int rt_n = ldb / 4, ct_n = Cp / 4;
+    const int ntile = rt_n * ct_n;
+    for (int t = threadIdx.x; t < ntile; t += NT) {
+        const int rt = t % rt_n, ct = t / rt_n;
+        const int r0 = rt * 4, c0 = ct * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int j = 0; j < C; ++j) {
+            const float4 tv = *reinterpret_cast<const float4*>(T + (size_t)j * ldb + r0);
+            float vv[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) vv[b] = V[(size_t)(c0 + b) * ldv + j];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                acc[0][b] = fmaf(tv.x, vv[b], acc[0][b]);
+                acc[1][b] = fmaf(tv.y, vv[b], acc[1][b]);
+                acc[2][b] = fmaf(tv.z, vv[b], acc[2][b]);
+                acc[3][b] = fmaf(tv.w, vv[b], acc[3][b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            *reinterpret_cast<float4*>(B + (size_t)(c0 + b) * ldb + r0) = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+    }
+    __syncthreads();
+}
+
+// V = I (Cp x Cp, stride ldv).
+__device__ inline void set_identity(float* V, int ldv, int Cp) {
+    for (int e = threadIdx.x; e < ldv * Cp; e += NT) {
+        const int r = e % ldv, c = e / ldv;
+        V[e] = (r == c) ? 1.f : 0.f;
+    }
+    __syncthreads();
+}
+
+// Singular values below this fraction of the largest are treated as converged noise
+// by the rotation test (FP32 dot products cannot resolve more).
+__device__ inline float jacobi_tol(int R) { return 2e-6f * fmaxf(1.f, sqrtf((float)R / 64.f)); }
+
+}  // namespace tilt

@@ -1,0 +1,180 @@
+// Kernels of the TILT-by-LADMAP solver for sm_103a and their host launchers.
+#include "tilt_launch.h"
+#include "tilt_solver.cuh"
+
+namespace tilt {
+
+// Copy a small POD record word by word into shared memory (all threads).
+template <typename T>
+__device__ inline void copy_to_shared(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "record size");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += NT) d[w] = s[w];
+    __syncthreads();
+}
+
+// One CTA per problem: the whole of Algorithm 1.  The result record and the completion
+// flag live in host-mapped memory, so the host sees every problem retire on its own.
+template <int MINB>
+__global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const int* order) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    __shared__ Problem sp;
+    __shared__ Result sres;
+    SmemLayout L = carve_smem(smem_raw);
+    copy_to_shared(&sp, probs + order[blockIdx.x]);
+    solve_problem(sp, L, sres);
+    if (threadIdx.x == 0) {
+        *sp.res = sres;
+        __threadfence_system();
+        *sp.done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) warp_step_kernel(WarpArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    const Dims d = make_dims(a.m, a.n, a.ttype);
+    k1_warp_jacobian(a.img, a.ld, a.H, a.W, d, a.ttype, a.tau, a.Dhat, a.J, L.sc);
+    if (threadIdx.x == 0) {
+        a.out->norm = L.sc->scal[0];
+        a.out->oob = L.sc->iscal[0];
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) gram_step_kernel(GramArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    const Dims d = make_dims(a.m, a.n, a.ttype);
+    const bool ok = k5_gram(d, a.ttype, a.tau, a.Dhat, a.J, L.sc);
+    if (threadIdx.x == 0) {
+        a.out->status = ok ? 0 : -2;
+        for (int k = 0; k < 3 * PMAX; ++k) a.out->Q[k] = L.sc->Q[k];
+        for (int k = 0; k < PMAX * PMAX; ++k) {
+            a.out->G[k] = L.sc->G[k];
+            a.out->Gi[k] = L.sc->Gi[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    const Dims d = make_dims(a.m, a.n, 0);
+    float *B, *V;
+    if (a.smem_svd) {
+        B = L.svd;
+        V = B + (size_t)d.ldb * d.Cp;
+    } else {
+        B = a.Bg;
+        V = a.Vg;
+    }
+    for (int e = threadIdx.x; e < d.ldb * d.Cp; e += NT) {
+        const int r = e % d.ldb, c = e / d.ldb;
+        B[e] = (r < d.R && c < d.C) ? a.M[(size_t)c * d.R + r] : 0.f;
+    }
+    __syncthreads();
+    set_identity(V, d.ldv, d.Cp);
+    const int sw = k2_jacobi(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag);
+    svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
+    const int nk = L.sc->iscal[1];
+    for (int e = threadIdx.x; e < d.S; e += NT) {
+        const int r = e % d.R, c = e / d.R;
+        float s = 0.f;
+        for (int q = 0; q < nk; ++q) {
+            const int k = L.kept[q];
+            s = fmaf(L.w[k] * B[(size_t)k * d.ldb + r], V[(size_t)k * d.ldv + c], s);
+        }
+        a.A[e] = s;
+    }
+    for (int k = threadIdx.x; k < d.C; k += NT) a.sigma[k] = L.sigma[k];
+    if (threadIdx.x == 0) a.out->sweeps = sw;
+}
+
+__global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    const Dims d = make_dims(a.m, a.n, a.ttype);
+    SvdBufs buf;
+    if (a.smem_svd) {
+        buf.B = L.svd;
+        buf.V = buf.B + (size_t)d.ldb * d.Cp;
+        buf.T = buf.V + (size_t)d.ldv * d.Cp;
+    } else {
+        buf.B = a.Bg;
+        buf.V = a.Vg;
+        buf.T = a.Tg;
+    }
+    {
+        const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+        for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }
+        for (size_t e = threadIdx.x; e < nv; e += NT) buf.V[e] = 0.f;
+        for (int e = threadIdx.x; e < d.S; e += NT) a.Mp[e] = 0.f;
+    }
+    __syncthreads();
+    if (!k5_gram(d, a.ttype, a.tau, a.Dhat, a.J, L.sc)) {
+        if (threadIdx.x == 0) a.out->status = -2;
+        return;
+    }
+    double mu0 = a.mu0;
+    if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(a.Dhat, d, L.sigma, L.w, L.sc);
+    const double lam = a.prm.lam > 0.0 ? a.prm.lam : 1.0 / sqrt((double)max(a.m, a.n));
+    bool haveV = false;
+    __shared__ Result cyc;
+    if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
+    __syncthreads();
+    InnerOut io = k_inner(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc);
+    if (threadIdx.x == 0) {
+        a.out->status = io.bad ? -1 : 0;
+        a.out->iters = io.iters;
+        a.out->sweeps = io.sweeps;
+        a.out->c1 = io.c1;
+        a.out->c2 = io.c2;
+        a.out->mu = io.mu_last;
+        for (int k = 0; k < PMAX; ++k) a.out->dtau[k] = k < a.ttype ? L.sc->cvec[k] : 0.0;
+    }
+}
+
+cudaError_t configure_kernels(size_t max_smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(solver_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(solver_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(svt_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(inner_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (minb >= 2)
+        solver_kernel<2><<<count, NT, smem, st>>>(probs, order);
+    else
+        solver_kernel<1><<<count, NT, smem, st>>>(probs, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_step(const WarpArgs& a, cudaStream_t st) {
+    warp_step_kernel<<<1, NT, smem_head_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_step(const GramArgs& a, cudaStream_t st) {
+    gram_step_kernel<<<1, NT, smem_head_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st) {
+    svt_step_kernel<<<1, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st) {
+    inner_step_kernel<<<1, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tilt

@@ -1,0 +1,80 @@
+// Host-side declarations of the kernel launchers (defined in tilt_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tilt_device.cuh"
+
+namespace tilt {
+
+// Output record of the step kernels (device memory).
+struct StepOut {
+    double norm;          // warp: ||D o tau||_F
+    int oob;              // warp: clamped samples
+    int sweeps;           // svt / inner
+    int iters;            // inner
+    int status;           // 0 ok, -2 singular G
+    double c1, c2, mu;    // inner
+    double Q[3 * PMAX], G[PMAX * PMAX], Gi[PMAX * PMAX];
+    double dtau[PMAX];
+};
+
+struct WarpArgs {
+    const float* img;
+    long long ld;
+    int H, W, m, n, ttype;
+    double tau[PMAX];
+    float* Dhat;
+    float* J;
+    StepOut* out;
+};
+
+struct GramArgs {
+    const float* J;
+    const float* Dhat;   // may be a zero plane (only J^T J and Q are reported)
+    int m, n, ttype;
+    double tau[PMAX];
+    StepOut* out;
+};
+
+struct SvtArgs {
+    const float* M;
+    float* A;
+    int m, n;
+    float eps;
+    int smem_svd;
+    float* Bg;    // global SVD buffers when !smem_svd
+    float* Vg;
+    float* Tg;
+    float* sigma; // device, C floats
+    StepOut* out;
+};
+
+struct InnerArgs {
+    const float* Dhat;
+    const float* J;
+    float* A;
+    float* E;
+    float* Y;
+    float* P;      // scratch S
+    float* Mp;     // scratch S
+    float* Bg;     // global SVD buffers when !smem_svd
+    float* Vg;
+    float* Tg;
+    int m, n, ttype, smem_svd;
+    double tau[PMAX];
+    Params prm;
+    double mu0;
+    StepOut* out;
+};
+
+// Solver: count CTAs, CTA b solves probs[order[b]].  minb selects the occupancy variant.
+cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st);
+cudaError_t launch_warp_step(const WarpArgs& a, cudaStream_t st);
+cudaError_t launch_gram_step(const GramArgs& a, cudaStream_t st);
+cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st);
+cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st);
+// One-time kernel attribute setup (dynamic shared memory opt-in).
+cudaError_t configure_kernels(size_t max_smem);
+
+}  // namespace tilt

@@ -1,0 +1,413 @@
+// Inner LADMAP loop (Sec. 3.2 with the reorganisations of Sec. 4.2-4.3) and the outer
+// loop of Algorithm 1, executed by one CTA per problem.
+#pragma once
+
+#include "tilt_device.cuh"
+
+namespace tilt {
+
+struct InnerOut {
+    int iters, sweeps, warm, rank;
+    bool converged, bad;
+    double c1, c2, mu_last, nuc, l1;
+};
+
+struct SvdBufs {
+    float* B;
+    float* V;
+    float* T;
+};
+
+__device__ inline unsigned long long clk() { return clock64(); }
+
+// Soft threshold T_eps(x) = sgn(x) max(|x| - eps, 0) (Sec. 3.2).
+__device__ inline float soft(float x, float eps) {
+    const float a = fabsf(x) - eps;
+    return a > 0.f ? copysignf(a, x) : 0.f;
+}
+
+// The inner loop.  Entry: A, E, Y hold the warm start (Eq. warm_start), sc->G/Gi/jd/scal[1]
+// hold J^T J + Q^T Q, its inverse, J^T D_hat and d0 = ||W^T W D_hat||_F (k5_gram).
+// Exit: A, E, Y the result; sc->cvec = G^-1 J^T (A + E - D_hat), i.e. dtau (Eq. Delta_tau).
+//
+// Iteration k (Eq. newvars2 with readings: +mu in the Y update, N centred at E_k, eta = 1):
+//   M = A - Y/mu - P                          (P = W^T W (A + E - D_hat) from iteration k-1)
+//   A' = S_{1/mu}(M)                          (K2 Jacobi SVD, warm from V, + reconstruction)
+//   P' = W^T W (A' + E - D_hat);  E' = T_{lam/mu}(E - Y/mu - P')
+//   P'' = W^T W (A' + E' - D_hat);  Y' = Y + mu P''
+//   c1 = ||P''|| / d0;  c2 = mu max(||A'-A||, ||E'-E||) / d0;  rho = rho0 if c2 < eps2 else 1
+//   stop when c1 < eps1 and c2 < eps2; mu <- min(mu_max, rho mu)
+// W^T W v = v - J (G^-1 (J^T v)); the J^T products of A' and E' are accumulated while
+// those planes are produced, so every W^T W costs one extra pass only.
+static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
+                            const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
+                            float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
+                            bool& haveV, const SmemLayout& L, Result* cyc) {
+    Scratch* sc = L.sc;
+    const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
+    InnerOut out;
+    out.iters = 0; out.sweeps = 0; out.warm = 0; out.rank = 0;
+    out.converged = false; out.bad = false;
+    out.c1 = out.c2 = 0.0; out.mu_last = mu0; out.nuc = 0.0; out.l1 = 0.0;
+    unsigned long long t0 = clk();
+
+    // ---- prologue: J^T A, J^T E, J^T Y; project Y (Eq. Y_new_warmstart); P_0; M_0
+    {
+        double acc[3 * PMAX];
+#pragma unroll
+        for (int k = 0; k < 3 * PMAX; ++k) acc[k] = 0.0;
+        for (int e = threadIdx.x; e < S; e += NT) {
+            const float a = A[e], ee = E[e], y = Y[e];
+#pragma unroll
+            for (int k = 0; k < PMAX; ++k) {
+                if (k < p) {
+                    const float jk = J[(size_t)k * S + e];
+                    acc[k] += (double)(jk * a);
+                    acc[PMAX + k] += (double)(jk * ee);
+                    acc[2 * PMAX + k] += (double)(jk * y);
+                }
+            }
+        }
+        block_sum<3 * PMAX>(acc, sc->red);
+        if (threadIdx.x == 0) {
+            double v[PMAX];
+            for (int k = 0; k < p; ++k) {
+                sc->ja[k] = acc[k];
+                sc->je[k] = acc[PMAX + k];
+                v[k] = acc[k] + acc[PMAX + k] - sc->jd[k];
+            }
+            ginv_apply(sc, p, v, sc->cvec);                         // c_P
+            for (int k = 0; k < p; ++k) v[k] = acc[2 * PMAX + k];
+            ginv_apply(sc, p, v, sc->dtau);                         // c_Y (temporary)
+        }
+        __syncthreads();
+        float cP[PMAX], cY[PMAX];
+#pragma unroll
+        for (int k = 0; k < PMAX; ++k) {
+            cP[k] = k < p ? (float)sc->cvec[k] : 0.f;
+            cY[k] = k < p ? (float)sc->dtau[k] : 0.f;
+        }
+        const float imu = (float)(1.0 / mu0);
+        double g[2] = {0.0, 0.0};
+        for (int e = threadIdx.x; e < S; e += NT) {
+            float jc = 0.f, jy = 0.f;
+#pragma unroll
+            for (int k = 0; k < PMAX; ++k) {
+                if (k < p) {
+                    const float jk = J[(size_t)k * S + e];
+                    jc = fmaf(jk, cP[k], jc);
+                    jy = fmaf(jk, cY[k], jy);
+                }
+            }
+            const float a = A[e];
+            const float y = Y[e] - jy;
+            const float pp = (a + E[e] - Dhat[e]) - jc;
+            Y[e] = y;
+            P[e] = pp;
+            const float mv = a - y * imu - pp;
+            const int r = e % R, c = e / R;
+            buf.T[(size_t)c * ldb + r] = mv;
+            const float mo = Mp[e];
+            g[0] += (double)((mv - mo) * (mv - mo));
+            g[1] += (double)(mv * mv);
+            Mp[e] = mv;
+        }
+        block_sum<2>(g, sc->red);
+        if (threadIdx.x == 0) { sc->scal[5] = g[0]; sc->scal[6] = g[1]; }
+        __syncthreads();
+    }
+    cyc->cyc_elem += clk() - t0;
+
+    const double d0 = sc->scal[1] > 0.0 ? sc->scal[1] : 1.0;
+    double mu = mu0;
+    for (int k = 1; k <= prm.max_inner; ++k) {
+        out.iters = k;
+        // ---- a6: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate)
+        t0 = clk();
+        const double dM2 = sc->scal[5], M2 = sc->scal[6];
+        const bool warm = haveV && (prm.eps_svd < 0.0 || dM2 < prm.eps_svd * prm.eps_svd * M2);
+        if (warm) {
+            gemm_TV(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
+            out.warm++;
+        } else {
+            float* t = buf.B; buf.B = buf.T; buf.T = t;
+            set_identity(buf.V, ldv, Cp);
+        }
+        const int sw = k2_jacobi(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag);
+        haveV = true;
+        out.sweeps += sw;
+        const float eps = (float)(1.0 / mu);
+        svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
+        unsigned long long t1 = clk();
+        cyc->cyc_svd += t1 - t0;
+
+        // ---- a7: A' = sum_kept w_k b_k v_k^T; ||A' - A||^2; J^T A'
+        const int nk = sc->iscal[1];
+        out.nuc = sc->scal[3];
+        out.rank = sc->iscal[2];
+        for (int q = threadIdx.x; q < nk * ldb; q += NT) {   // pre-scale kept columns by w_k
+            const int kq = L.kept[q / ldb];
+            buf.B[(size_t)kq * ldb + (q % ldb)] *= L.w[kq];
+        }
+        __syncthreads();
+        {
+            float acc[1 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
+            for (int e = threadIdx.x; e < S; e += NT) {
+                const int r = e % R, c = e / R;
+                float s = 0.f;
+                for (int q = 0; q < nk; ++q) {
+                    const int kq = L.kept[q];
+                    s = fmaf(buf.B[(size_t)kq * ldb + r], buf.V[(size_t)kq * ldv + c], s);
+                }
+                const float da = s - A[e];
+                acc[0] = fmaf(da, da, acc[0]);
+                A[e] = s;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2)
+                    if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], s, acc[1 + k2]);
+            }
+            double dacc[1 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 1 + PMAX; ++k2) dacc[k2] = acc[k2];
+            block_sum<1 + PMAX>(dacc, sc->red);
+            if (threadIdx.x == 0) {
+                sc->scal[7] = dacc[0];
+                double v[PMAX];
+                for (int k2 = 0; k2 < p; ++k2) {
+                    sc->ja[k2] = dacc[1 + k2];
+                    v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
+                }
+                ginv_apply(sc, p, v, sc->cvec);                       // c'
+            }
+            __syncthreads();
+        }
+        unsigned long long t2 = clk();
+        cyc->cyc_recon += t2 - t1;
+
+        // ---- a8: E' = T_{lam/mu}(E - Y/mu - W^T W (A' + E - D_hat)); ||E' - E||^2; J^T E'; ||E'||_1
+        const float imu = (float)(1.0 / mu);
+        const float thr = (float)(lam / mu);
+        {
+            float cc[PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
+            float acc[2 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 2 + PMAX; ++k2) acc[k2] = 0.f;
+            for (int e = threadIdx.x; e < S; e += NT) {
+                float jv[PMAX];
+                float jc = 0.f;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) {
+                    jv[k2] = k2 < p ? J[(size_t)k2 * S + e] : 0.f;
+                    jc = fmaf(jv[k2], cc[k2], jc);
+                }
+                const float ee = E[e];
+                const float p1 = (A[e] + ee - Dhat[e]) - jc;
+                const float nv = ee - Y[e] * imu - p1;
+                const float en = soft(nv, thr);
+                const float de = en - ee;
+                acc[0] = fmaf(de, de, acc[0]);
+                acc[1] += fabsf(en);
+                E[e] = en;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) acc[2 + k2] = fmaf(jv[k2], en, acc[2 + k2]);
+            }
+            double dacc[2 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 2 + PMAX; ++k2) dacc[k2] = acc[k2];
+            block_sum<2 + PMAX>(dacc, sc->red);
+            if (threadIdx.x == 0) {
+                sc->scal[8] = dacc[0];
+                sc->scal[9] = dacc[1];
+                double v[PMAX];
+                for (int k2 = 0; k2 < p; ++k2) {
+                    sc->je[k2] = dacc[2 + k2];
+                    v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
+                }
+                ginv_apply(sc, p, v, sc->cvec);                       // c'' (= dtau at exit)
+            }
+            __syncthreads();
+        }
+        const double dA = sqrt(sc->scal[7]), dE = sqrt(sc->scal[8]);
+        out.l1 = sc->scal[9];
+        const double c2 = mu * fmax(dA, dE) / d0;
+        const double rho = (c2 < prm.eps2) ? prm.rho0 : 1.0;
+        const double mu_next = fmin(prm.mu_max, rho * mu);
+
+        // ---- a9: P'' = W^T W (A' + E' - D_hat); Y' = Y + mu P''; next M = A' - Y'/mu_next - P''
+        {
+            float cc[PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
+            const float muf = (float)mu;
+            const float imun = (float)(1.0 / mu_next);
+            float acc[3] = {0.f, 0.f, 0.f};
+            for (int e = threadIdx.x; e < S; e += NT) {
+                float jc = 0.f;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2)
+                    if (k2 < p) jc = fmaf(J[(size_t)k2 * S + e], cc[k2], jc);
+                const float a = A[e];
+                const float pp = (a + E[e] - Dhat[e]) - jc;
+                const float y = fmaf(muf, pp, Y[e]);
+                Y[e] = y;
+                P[e] = pp;
+                acc[0] = fmaf(pp, pp, acc[0]);
+                const float mv = a - y * imun - pp;
+                const int r = e % R, c = e / R;
+                buf.T[(size_t)c * ldb + r] = mv;
+                const float mo = Mp[e];
+                acc[1] = fmaf(mv - mo, mv - mo, acc[1]);
+                acc[2] = fmaf(mv, mv, acc[2]);
+                Mp[e] = mv;
+            }
+            double dacc[3] = {acc[0], acc[1], acc[2]};
+            block_sum<3>(dacc, sc->red);
+            if (threadIdx.x == 0) {
+                sc->scal[10] = dacc[0];
+                sc->scal[5] = dacc[1];
+                sc->scal[6] = dacc[2];
+            }
+            __syncthreads();
+        }
+        cyc->cyc_elem += clk() - t2;
+        const double c1 = sqrt(sc->scal[10]) / d0;
+        out.c1 = c1;
+        out.c2 = c2;
+        out.mu_last = mu;
+        if (!isfinite(c1) || !isfinite(c2)) {
+            out.bad = true;
+            break;
+        }
+        if (c1 < prm.eps1 && c2 < prm.eps2) {
+            out.converged = true;
+            break;
+        }
+        mu = mu_next;
+    }
+    return out;
+}
+
+// Largest corner displacement (pixels) between tau and tau + dtau (outer stopping rule).
+__device__ inline double corner_shift(const double* tau, const double* dtau, int ttype, int m, int n, int p) {
+    const double a = 0.5 * (n - 1), b = 0.5 * (m - 1);
+    const double cu[4] = {-a, a, a, -a}, cv[4] = {-b, -b, b, b};
+    double t1[PMAX];
+    for (int k = 0; k < PMAX; ++k) t1[k] = k < p ? tau[k] + dtau[k] : 0.0;
+    double mx = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        MapPt q0 = map_point(tau, ttype, cu[c], cv[c]);
+        MapPt q1 = map_point(t1, ttype, cu[c], cv[c]);
+        mx = fmax(mx, hypot(q1.x - q0.x, q1.y - q0.y));
+    }
+    return mx;
+}
+
+// Algorithm 1 for one problem.
+static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Result& res) {
+    Scratch* sc = L.sc;
+    const Dims d = make_dims(pr.m, pr.n, pr.p);
+    const Params& prm = pr.prm;
+    const int S = d.S;
+    SvdBufs buf;
+    if (pr.smem_svd) {
+        buf.B = L.svd;
+        buf.V = buf.B + (size_t)d.ldb * d.Cp;
+        buf.T = buf.V + (size_t)d.ldv * d.Cp;
+    } else {
+        buf.B = pr.pl.Bg;
+        buf.V = pr.pl.Vg;
+        buf.T = pr.pl.Tg;
+    }
+    // zero the SVD buffers (padding rows/columns are read by the tiled GEMM)
+    {
+        const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+        for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }
+        for (size_t e = threadIdx.x; e < nv; e += NT) buf.V[e] = 0.f;
+    }
+    const double lam = prm.lam > 0.0 ? prm.lam : 1.0 / sqrt((double)max(pr.m, pr.n));
+    if (threadIdx.x < PMAX) sc->tau[threadIdx.x] = threadIdx.x < pr.p ? pr.tau[threadIdx.x] : 0.0;
+    res.cyc_warp = res.cyc_svd = res.cyc_recon = res.cyc_elem = res.cyc_other = 0;
+    __syncthreads();
+
+    int status = 1;
+    bool inner_maxed = false;
+    int outer = 0, inner_total = 0, sweeps = 0, warm = 0, rank = 0;
+    double c1 = 0.0, nuc = 0.0, l1 = 0.0;
+    bool haveV = false;
+
+    unsigned long long t0 = clk();
+    k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
+    res.cyc_warp += clk() - t0;
+    if (!(sc->scal[0] > 0.0)) {
+        status = -3;
+    } else {
+        for (int e = threadIdx.x; e < S; e += NT) {     // A_0 = D_hat (R9), E_0 = Y_0 = 0
+            pr.pl.A[e] = pr.pl.Dhat[e];
+            pr.pl.E[e] = 0.f;
+            pr.pl.Y[e] = 0.f;
+            pr.pl.Mp[e] = 0.f;
+        }
+        __syncthreads();
+        for (outer = 1; outer <= prm.max_outer; ++outer) {
+            t0 = clk();
+            if (outer > 1) {
+                k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
+                if (!(sc->scal[0] > 0.0)) { status = -3; break; }
+            }
+            unsigned long long t1 = clk();
+            res.cyc_warp += t1 - t0;
+            if (!k5_gram(d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc)) { status = -2; break; }
+            double mu0 = prm.mu0;
+            if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
+            res.cyc_other += clk() - t1;
+            InnerOut io = k_inner(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
+                                  pr.pl.Mp, buf, haveV, L, &res);
+            inner_total += io.iters;
+            sweeps += io.sweeps;
+            warm += io.warm;
+            c1 = io.c1; nuc = io.nuc; l1 = io.l1; rank = io.rank;
+            if (io.bad) { status = -1; break; }
+            if (!io.converged) inner_maxed = true;
+            // Steps 3-4: dtau = G^-1 J^T (A + E - D_hat) (= sc->cvec), tau <- tau + dtau
+            if (threadIdx.x == 0) {
+                double dt[PMAX];
+                for (int k = 0; k < PMAX; ++k) dt[k] = k < pr.p ? sc->cvec[k] : 0.0;
+                const double sh = corner_shift(sc->tau, dt, pr.ttype, pr.m, pr.n, pr.p);
+                bool fin = isfinite(sh);
+                for (int k = 0; k < pr.p; ++k) {
+                    sc->tau[k] += dt[k];
+                    fin = fin && isfinite(sc->tau[k]);
+                }
+                sc->scal[11] = fin ? sh : -1.0;
+            }
+            __syncthreads();
+            const double sh = sc->scal[11];
+            __syncthreads();
+            if (sh < 0.0) { status = -1; break; }
+            if (sh < prm.outer_tol) { status = 0; break; }
+        }
+        if (outer > prm.max_outer) outer = prm.max_outer;
+    }
+    if (status >= 0 && inner_maxed) status = 2;
+    if (threadIdx.x == 0) {
+        res.status = status;
+        res.p = pr.p;
+        for (int k = 0; k < 8; ++k) res.tau[k] = k < pr.p ? sc->tau[k] : 0.0;
+        res.objective = nuc + lam * l1;
+        res.lambda = lam;
+        res.rank_A = rank;
+        res.outer_iters = outer;
+        res.inner_iters = inner_total;
+        res.svd_sweeps = sweeps;
+        res.svd_warm = warm;
+        res.oob_pixels = sc->iscal[0];
+        res.kkt_residual = c1;
+    }
+    __syncthreads();
+}
+
+}  // namespace tilt
