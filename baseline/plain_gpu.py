@@ -1,0 +1,127 @@
+"""Plain GPU solver: the comparison arm of the benchmark, not the product path.
+
+The same method as the library (Algorithm 1 with the inner LADMAP loop in the W^T W form of
+Sec. 4.3, the same readings and parameters), written the straightforward way: one patch at
+a time, PyTorch tensor operations in FP32 on the GPU, a cuSOLVER SVD (torch.linalg.svd) for
+every singular value thresholding, and the stopping tests evaluated on the host after every
+inner iteration.  It shares no code with the CUDA library or with the oracle.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+
+def _map(tau, ttype, U, V):
+    t = [float(x) for x in tau]
+    x = t[0] * U + t[1] * V + t[2]
+    y = t[3] * U + t[4] * V + t[5]
+    one = torch.ones_like(U)
+    zero = torch.zeros_like(U)
+    if ttype == 8:
+        den = t[6] * U + t[7] * V + 1.0
+        x = x / den
+        y = y / den
+        dx = [U / den, V / den, one / den, zero, zero, zero, -x * U / den, -x * V / den]
+        dy = [zero, zero, zero, U / den, V / den, one / den, -y * U / den, -y * V / den]
+    else:
+        dx = [U, V, one, zero, zero, zero]
+        dy = [zero, zero, zero, U, V, one]
+    return x, y, dx, dy
+
+
+def warp_jacobian(img, tau, ttype, m, n):
+    dev = img.device
+    H, W = img.shape
+    v = torch.arange(m, dtype=torch.float64, device=dev) - (m - 1) / 2.0
+    u = torch.arange(n, dtype=torch.float64, device=dev) - (n - 1) / 2.0
+    V, U = torch.meshgrid(v, u, indexing="ij")
+    x, y, dx, dy = _map(tau, ttype, U, V)
+    inx = (x >= 0) & (x <= W - 1)
+    iny = (y >= 0) & (y <= H - 1)
+    xc = x.clamp(0, W - 1)
+    yc = y.clamp(0, H - 1)
+    x0 = torch.minimum(torch.floor(xc), torch.tensor(W - 2.0, device=dev))
+    y0 = torch.minimum(torch.floor(yc), torch.tensor(H - 2.0, device=dev))
+    fx = (xc - x0).float()
+    fy = (yc - y0).float()
+    xi = x0.long()
+    yi = y0.long()
+    I00, I01 = img[yi, xi], img[yi, xi + 1]
+    I10, I11 = img[yi + 1, xi], img[yi + 1, xi + 1]
+    val = (1 - fy) * ((1 - fx) * I00 + fx * I01) + fy * ((1 - fx) * I10 + fx * I11)
+    gx = torch.where(inx, (1 - fy) * (I01 - I00) + fy * (I11 - I10), torch.zeros_like(val))
+    gy = torch.where(iny, (1 - fx) * (I10 - I00) + fx * (I11 - I01), torch.zeros_like(val))
+    Jraw = torch.stack([gx * a.float() + gy * b.float() for a, b in zip(dx, dy)], dim=-1).reshape(m * n, -1)
+    s = torch.linalg.vector_norm(val.double())
+    Dhat = (val.double() / s).float()
+    d = Dhat.reshape(-1)
+    J = ((Jraw - torch.outer(d, d @ Jraw)) / s.float())
+    return Dhat, J
+
+
+def constraint_rows(tau, ttype, m, n):
+    a, b = (n - 1) / 2.0, (m - 1) / 2.0
+    U = torch.tensor([-a, a, a, -a], dtype=torch.float64)
+    V = torch.tensor([-b, -b, b, b], dtype=torch.float64)
+    x, y, dx, dy = _map(tau, ttype, U, V)
+    dx = torch.stack(dx, dim=-1)
+    dy = torch.stack(dy, dim=-1)
+    xn, yn = torch.roll(x, -1), torch.roll(y, -1)
+    dxn, dyn = torch.roll(dx, -1, 0), torch.roll(dy, -1, 0)
+    da = 0.5 * (dx * yn[:, None] + x[:, None] * dyn - dxn * y[:, None] - xn[:, None] * dy).sum(0)
+    return torch.stack([dx.mean(0), dy.mean(0), da / ((m - 1) * (n - 1))]).numpy()
+
+
+def tilt_plain(img, tau0, ttype, m, n, eps1=1e-6, eps2=0.1, rho0=1.5, mu_max=1e10, max_inner=500,
+               max_outer=10, outer_tol=1e-2):
+    lam = 1.0 / math.sqrt(max(m, n))
+    tau = np.array(tau0, dtype=np.float64)
+    Dhat, J = warp_jacobian(img, tau, ttype, m, n)
+    A = Dhat.clone()
+    E = torch.zeros_like(A)
+    Y = torch.zeros_like(A)
+    inner_total = 0
+    for outer in range(1, max_outer + 1):
+        if outer > 1:
+            Dhat, J = warp_jacobian(img, tau, ttype, m, n)
+        Q = constraint_rows(tau, ttype, m, n)
+        G = (J.double().T @ J.double()).cpu().numpy() + Q.T @ Q
+        Gi = torch.from_numpy(np.linalg.inv(G)).float().to(img.device)
+
+        def wtw(X):
+            x = X.reshape(-1)
+            return (x - J @ (Gi @ (J.T @ x))).reshape(X.shape)
+
+        Y = wtw(Y)
+        d0 = float(torch.linalg.vector_norm(wtw(Dhat)))
+        mu = 1.25 / float(torch.linalg.matrix_norm(Dhat, ord=2))
+        P = wtw(A + E - Dhat)
+        for k in range(max_inner):
+            M = A - Y / mu - P
+            Uf, S, Vh = torch.linalg.svd(M, full_matrices=False)
+            A1 = (Uf * torch.clamp(S - 1.0 / mu, min=0)) @ Vh
+            P1 = wtw(A1 + E - Dhat)
+            N = E - Y / mu - P1
+            E1 = torch.sign(N) * torch.clamp(N.abs() - lam / mu, min=0)
+            P2 = wtw(A1 + E1 - Dhat)
+            Y = Y + mu * P2
+            c1 = float(torch.linalg.vector_norm(P2)) / d0
+            c2 = mu * max(float(torch.linalg.vector_norm(A1 - A)), float(torch.linalg.vector_norm(E1 - E))) / d0
+            A, E, P = A1, E1, P2
+            inner_total += 1
+            if c1 < eps1 and c2 < eps2:
+                break
+            mu = min(mu_max, (rho0 if c2 < eps2 else 1.0) * mu)
+        dtau = (Gi.double() @ (J.double().T @ (A + E - Dhat).reshape(-1).double())).cpu().numpy()
+        a, b = (n - 1) / 2.0, (m - 1) / 2.0
+        U = torch.tensor([-a, a, a, -a], dtype=torch.float64)
+        V = torch.tensor([-b, -b, b, b], dtype=torch.float64)
+        x0, y0, _, _ = _map(tau, ttype, U, V)
+        x1, y1, _, _ = _map(tau + dtau, ttype, U, V)
+        tau = tau + dtau
+        if float(torch.max(torch.hypot(x1 - x0, y1 - y0))) < outer_tol:
+            break
+    return tau, inner_total

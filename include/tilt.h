@@ -64,7 +64,7 @@ typedef struct {
  * a value <= 0 in lambda or mu0 selects the default rule. */
 typedef struct {
     double lambda;     /* weight of ||E||_1; <= 0 -> 1/sqrt(max(m, n))                        */
-    double eps1;       /* Eq. Cond1 threshold (default 1e-6)                                  */
+    double eps1;       /* Eq. Cond1 threshold (default 1e-5)                                  */
     double eps2;       /* Eq. Cond2 / Eq. rho threshold (default 0.1)                         */
     double rho0;       /* Eq. rho growth factor, >= 1 (default 1.5)                           */
     double mu0;        /* initial penalty of every inner loop; <= 0 -> 1.25 / ||D_hat||_2     */
@@ -94,6 +94,9 @@ typedef struct {
     int oob_pixels;      /* samples clamped to the image edge in the last warp                */
     double kkt_residual; /* last Eq. Cond1 value                                              */
     float latency_ms;    /* submit -> completion, host clock                                  */
+    uint64_t phase_cycles[5]; /* SM clock cycles of the solve by phase: warp + Jacobian, SVD
+                                 (Jacobi sweeps + warm-start product), SVT reconstruction,
+                                 elementwise passes (E, Y, M), other (Gram, ||D||_2)          */
 } tilt_result;
 
 /* Fill *p with the default parameters. */
@@ -155,6 +158,12 @@ const char* tilt_last_error(tilt_ctx* ctx);
 
 /* Number of device kernels this context has launched (for launch accounting). */
 uint64_t tilt_kernel_launches(tilt_ctx* ctx);
+
+/* Device time of the grouped launches of the most recent tilt_submit_batch, measured with
+ * CUDA events recorded around each launch on its own stream.  Waits (bounded, 600 s) for
+ * those launches to finish, writes up to cap elapsed times in milliseconds to ms_out (one
+ * per occupancy class launched) and returns their number, or a negative tilt_status. */
+int tilt_batch_kernel_ms(tilt_ctx* ctx, float* ms_out, int cap);
 
 /* ------------------------------------------------------------------------------------------
  * Step-level entry points.  They run one step of the method on one problem with the same

@@ -39,7 +39,7 @@ design notes of the repository):
 * R7  mu_0 = 1.25 / ||D_hat||_2, reset at every outer step (Algorithm 1 lists mu_0 among
       the initial conditions of each inner loop); mu_max = 1e10; rho_0 = 1.5 and
       eps_2 = 0.1 (the rho rule of Eq. rho only lets mu grow while c2 < eps_2, so a small
-      eps_2 freezes mu); eps_1 = 1e-6; the Cond1 denominator and numerator use W^T W (the
+      eps_2 freezes mu); eps_1 = 1e-5; the Cond1 denominator and numerator use W^T W (the
       operator the iteration carries) in place of J_perp.
 * R8  The outer loop stops when dtau moves no corner of the window by more than
       outer_tol pixels, or after max_outer steps.
@@ -63,7 +63,7 @@ class Params:
     """Solver parameters (Algorithm 1 inputs; values the paper leaves open are readings)."""
 
     lam: float = -1.0            # <= 0 -> 1/sqrt(max(m, n))
-    eps1: float = 1e-6           # Cond1 threshold
+    eps1: float = 1e-5           # Cond1 threshold
     eps2: float = 0.1            # Cond2 / rho threshold
     rho0: float = 1.5
     mu0: float = -1.0            # <= 0 -> 1.25/||D_hat||_2

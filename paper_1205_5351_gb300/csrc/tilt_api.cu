@@ -92,7 +92,7 @@ private:
 };
 
 struct Layout {   // byte offsets inside one problem's workspace
-    size_t dhat, j, a, e, y, p, mp, bg, vg, tg, img, order, total;
+    size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, order, total;
     int smem_svd, minb;
     size_t smem;
 };
@@ -151,6 +151,8 @@ struct tilt_ctx {
     size_t scratch_bytes = 0;
     StepOut* step_out = nullptr;    // host-mapped
     StepOut* step_out_dev = nullptr;
+    cudaEvent_t ev[6] = {};         // start/end events of the last grouped launches (3 classes)
+    int ev_used = 0;
 };
 
 namespace {
@@ -191,6 +193,7 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.y = take(S);
     L.p = take(S);
     L.mp = take(S);
+    L.zg = take((size_t)d.C * d.C * sizeof(float));
     const size_t svd = svd_smem_bytes(d);
     const size_t head = smem_head_bytes();
     L.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
@@ -256,6 +259,7 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.pl.Y = reinterpret_cast<float*>(base + L.y);
     pr.pl.P = reinterpret_cast<float*>(base + L.p);
     pr.pl.Mp = reinterpret_cast<float*>(base + L.mp);
+    pr.pl.Zg = reinterpret_cast<float*>(base + L.zg);
     if (!L.smem_svd) {
         pr.pl.Bg = reinterpret_cast<float*>(base + L.bg);
         pr.pl.Vg = reinterpret_cast<float*>(base + L.vg);
@@ -328,6 +332,11 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->oob_pixels = r.oob_pixels;
     out->kkt_residual = r.kkt_residual;
     out->latency_ms = (float)(t.t_done - t.t_submit);
+    out->phase_cycles[0] = r.cyc_warp;
+    out->phase_cycles[1] = r.cyc_svd;
+    out->phase_cycles[2] = r.cyc_recon;
+    out->phase_cycles[3] = r.cyc_elem;
+    out->phase_cycles[4] = r.cyc_other;
 }
 
 // Copy a device plane (long-side-contiguous) to a host m x n row-major array.
@@ -373,7 +382,7 @@ extern "C" {
 void tilt_default_params(tilt_params* p) {
     if (!p) return;
     p->lambda = -1.0;
-    p->eps1 = 1e-6;
+    p->eps1 = 1e-5;
     p->eps2 = 0.1;
     p->rho0 = 1.5;
     p->mu0 = -1.0;
@@ -419,6 +428,7 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->res_dev, ctx->res, 0));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->done_dev, ctx->done, 0));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->step_out_dev, ctx->step_out, 0));
+    for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
     memset(ctx->done, 0, ns * sizeof(int));
     ctx->free_slots.reserve(ns);
     for (int s = (int)ns - 1; s >= 0; --s) ctx->free_slots.push_back(s);
@@ -570,7 +580,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
     // the order array is copied once (pageable source: staged before the call returns)
     CUDA_TRY(cudaMemcpyAsync(ord_dev, ord_slots.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st[0]));
     CUDA_TRY(cudaStreamSynchronize(st[0]));
-    int start = 0;
+    int start = 0, nev = 0;
     while (start < count) {
         const int c = cls(idx[start]);
         int end = start;
@@ -580,11 +590,30 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
             ++end;
         }
         const int minb = (c == 0) ? 2 : 1;
+        if (nev < 3) CUDA_TRY(cudaEventRecord(ctx->ev[2 * nev], st[c]));
         CUDA_TRY(launch_solver(ctx->probs_dev, ord_dev + start, end - start, minb, smem, st[c]));
+        if (nev < 3) { CUDA_TRY(cudaEventRecord(ctx->ev[2 * nev + 1], st[c])); ++nev; }
         ctx->launches++;
         start = end;
     }
+    ctx->ev_used = nev;
     return TILT_OK;
+}
+
+int tilt_batch_kernel_ms(tilt_ctx* ctx, float* ms_out, int cap) {
+    if (!ctx || (cap > 0 && !ms_out)) return fail(TILT_E_INVAL, "bad arguments");
+    const double t_end = now_ms() + 600000.0;
+    int n = 0;
+    for (int q = 0; q < ctx->ev_used && n < cap; ++q) {
+        while (cudaEventQuery(ctx->ev[2 * q + 1]) == cudaErrorNotReady) {
+            if (now_ms() > t_end) return fail(TILT_E_TIMEOUT, "grouped launch still running");
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev[2 * q], ctx->ev[2 * q + 1]));
+        ms_out[n++] = ms;
+    }
+    return n;
 }
 
 int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, float* E_out) {
@@ -642,6 +671,7 @@ int tilt_destroy(tilt_ctx* ctx) {
     }
     for (auto s : ctx->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(ctx->copy_stream);
+    for (auto e : ctx->ev) cudaEventDestroy(e);
     cudaFree(ctx->pool_base);
     if (ctx->scratch) cudaFree(ctx->scratch);
     cudaFreeHost(ctx->probs);
@@ -716,13 +746,15 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
     a.m = m; a.n = n; a.eps = eps;
     a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-    const size_t need = sizeof(float) * (a.smem_svd ? 0 : (2 * nb + nv)) + sizeof(float) * MAX_SIDE;
+    const size_t nz = (size_t)d.C * d.C;
+    const size_t need = sizeof(float) * ((a.smem_svd ? 0 : (2 * nb + nv)) + MAX_SIDE + ((nz + 63) & ~(size_t)63));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
     float* s = reinterpret_cast<float*>(ctx->scratch);
     a.sigma = s;
+    a.Zg = s + MAX_SIDE;
     if (!a.smem_svd) {
-        a.Bg = s + MAX_SIDE;
+        a.Bg = a.Zg + ((nz + 63) & ~(size_t)63);
         a.Vg = a.Bg + nb;
         a.Tg = a.Vg + nv;
     }
@@ -748,14 +780,16 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
     a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-    const size_t need = sizeof(float) * (2 * (size_t)d.S + (a.smem_svd ? 0 : (2 * nb + nv)));
+    const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.C + 63) & ~(size_t)63;
+    const size_t need = sizeof(float) * (2 * S4 + nz + (a.smem_svd ? 0 : (2 * nb + nv)));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
     float* s = reinterpret_cast<float*>(ctx->scratch);
     a.P = s;
-    a.Mp = s + d.S;
+    a.Mp = s + S4;
+    a.Zg = a.Mp + S4;
     if (!a.smem_svd) {
-        a.Bg = a.Mp + d.S;
+        a.Bg = a.Zg + nz;
         a.Vg = a.Bg + nb;
         a.Tg = a.Vg + nv;
     }

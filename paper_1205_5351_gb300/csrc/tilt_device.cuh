@@ -50,6 +50,7 @@ struct Planes {
     float* Bg;     // ldb * Cp  (SVD work, global mode only)
     float* Vg;     // ldv * Cp
     float* Tg;     // ldb * Cp
+    float* Zg;     // C * C    (X^T b_k of the kept columns, for the reconstruction)
 };
 
 // One problem as the solver kernel sees it.
@@ -93,7 +94,7 @@ __host__ __device__ inline size_t svd_smem_bytes(const Dims& d) {
 // ------------------------------------------------------------------------------ CTA scratch
 // Small per-CTA scalars kept in shared memory.
 struct Scratch {
-    double red[16 * NW];       // block-reduction staging
+    double red[48 * NW];       // block-reduction staging (up to 48 values per reduction)
     double G[PMAX * PMAX];     // J^T J + Q^T Q
     double Gi[PMAX * PMAX];    // its inverse
     double Q[3 * PMAX];
@@ -138,6 +139,7 @@ __device__ inline SmemLayout carve_smem(unsigned char* base) {
 // Sum K doubles over the CTA; every thread gets the totals.  Fixed order -> deterministic.
 template <int K>
 __device__ inline void block_sum(double (&v)[K], double* red) {
+    static_assert(K <= 48, "block_sum staging holds 48 values per warp");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -489,21 +491,26 @@ static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int
                 b = warp_sum(b);
                 g = warp_sum(g);
                 if (fabsf(g) > tol * sqrtf(a) * sqrtf(b)) {
+                    // rotation angle from the 2 x 2 Gram matrix [[a, g], [g, b]]; applied in
+                    // Rutishauser's form x' = x - s (y + r x), y' = y + s (x - r y) with
+                    // r = tan(theta/2), so that small angles do not inflate the column norms
+                    // (with c rounded to 1 the plain form grows them by t^2/2 per rotation)
                     const float zeta = (b - a) / (2.f * g);
                     const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
                     const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
                     const float s = c * t;
+                    const float rr = s / (1.f + c);
                     for (int r = lane; r < R; r += 32) {
                         const float x = bi[r], y = bj[r];
-                        bi[r] = c * x - s * y;
-                        bj[r] = s * x + c * y;
+                        bi[r] = x - s * fmaf(rr, x, y);
+                        bj[r] = y + s * fmaf(-rr, y, x);
                     }
                     float* vi = V + (size_t)i * ldv;
                     float* vj = V + (size_t)j * ldv;
                     for (int r = lane; r < C; r += 32) {
                         const float x = vi[r], y = vj[r];
-                        vi[r] = c * x - s * y;
-                        vj[r] = s * x + c * y;
+                        vi[r] = x - s * fmaf(rr, x, y);
+                        vj[r] = y + s * fmaf(-rr, y, x);
                     }
                     rotated = true;
                 }
@@ -560,6 +567,32 @@ static __device__ void svt_weights(const float* B, int ldb, int R, int C, float 
     __syncthreads();
 }
 
+// Reconstruction coefficients of the singular value thresholding from the left factor:
+// with B = U Sigma (orthogonal columns after the sweeps) and X = B V^T,
+//   S_eps(X) = sum_k (sigma_k - eps)_+ u_k v_k^T = sum_k (w_k / sigma_k^2) b_k (X^T b_k)^T,
+// which needs only the measured orthogonality of B, not the orthogonality of the
+// accumulated V (FP32 rotations drift V away from orthogonal far faster than B).
+// Z[q*C + c] = (w_k / sigma_k^2) (X^T b_k)_c for the kept columns k = kept[q].
+static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb, int R,
+                                       int C, const float* sigma, const float* w, const int* kept, int nk,
+                                       float* __restrict__ Z) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int idx = warp; idx < nk * C; idx += NW) {
+        const int q = idx / C, c = idx - q * C;
+        const int k = kept[q];
+        const float* x = X + (size_t)c * ldx;
+        const float* b = B + (size_t)k * ldb;
+        float s = 0.f;
+        for (int r = lane; r < R; r += 32) s = fmaf(x[r], b[r], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            const float sg = sigma[k];
+            Z[(size_t)q * C + c] = s * (w[k] / (sg * sg));
+        }
+    }
+    __syncthreads();
+}
+
 // B = T V (R x C times C x C), 4 x 4 register tiles; T, B stride ldb (multiple of 4),
 // V stride ldv.  Works on padded sizes (ldb rows, Cp columns).
 static __device__ void gemm_TV(const float* __restrict__ T, int ldb, const float* __restrict__ V, int ldv, float* __restrict__ B,
@@ -594,6 +627,29 @@ static __device__ void gemm_TV(const float* __restrict__ T, int ldb, const float
     __syncthreads();
 }
 
+// Largest deviation of a column norm of V from 1 (how far the FP32 rotations have let V
+// drift from orthogonal).
+static __device__ float v_drift(const float* V, int ldv, int C, Scratch* sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float mx = 0.f;
+    for (int k = warp; k < C; k += NW) {
+        const float* v = V + (size_t)k * ldv;
+        float s = 0.f;
+        for (int r = lane; r < C; r += 32) s = fmaf(v[r], v[r], s);
+        s = warp_sum(s);
+        mx = fmaxf(mx, fabsf(s - 1.f));
+    }
+    double m[1] = {0.0};
+    // max via the sum machinery: reduce max per warp through shared memory
+    if (lane == 0) sc->red[warp] = mx;
+    __syncthreads();
+    float r = 0.f;
+    for (int w = 0; w < NW; ++w) r = fmaxf(r, (float)sc->red[w]);
+    __syncthreads();
+    (void)m;
+    return r;
+}
+
 // V = I (Cp x Cp, stride ldv).
 __device__ inline void set_identity(float* V, int ldv, int Cp) {
     for (int e = threadIdx.x; e < ldv * Cp; e += NT) {
@@ -605,6 +661,6 @@ __device__ inline void set_identity(float* V, int ldv, int Cp) {
 
 // Singular values below this fraction of the largest are treated as converged noise
 // by the rotation test (FP32 dot products cannot resolve more).
-__device__ inline float jacobi_tol(int R) { return 2e-6f * fmaxf(1.f, sqrtf((float)R / 64.f)); }
+__device__ inline float jacobi_tol(int R) { return 1e-6f * fmaxf(1.f, sqrtf((float)R / 256.f)); }
 
 }  // namespace tilt

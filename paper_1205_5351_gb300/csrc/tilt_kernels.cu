@@ -78,13 +78,11 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     const int sw = k2_jacobi(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag);
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
+    svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg);
     for (int e = threadIdx.x; e < d.S; e += NT) {
         const int r = e % d.R, c = e / d.R;
         float s = 0.f;
-        for (int q = 0; q < nk; ++q) {
-            const int k = L.kept[q];
-            s = fmaf(L.w[k] * B[(size_t)k * d.ldb + r], V[(size_t)k * d.ldv + c], s);
-        }
+        for (int q = 0; q < nk; ++q) s = fmaf(B[(size_t)L.kept[q] * d.ldb + r], a.Zg[(size_t)q * d.C + c], s);
         a.A[e] = s;
     }
     for (int k = threadIdx.x; k < d.C; k += NT) a.sigma[k] = L.sigma[k];
@@ -105,6 +103,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
         buf.V = a.Vg;
         buf.T = a.Tg;
     }
+    buf.Z = a.Zg;
     {
         const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
         for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }

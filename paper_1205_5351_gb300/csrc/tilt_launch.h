@@ -46,6 +46,7 @@ struct SvtArgs {
     float* Bg;    // global SVD buffers when !smem_svd
     float* Vg;
     float* Tg;
+    float* Zg;    // device, C * C floats
     float* sigma; // device, C floats
     StepOut* out;
 };
@@ -61,6 +62,7 @@ struct InnerArgs {
     float* Bg;     // global SVD buffers when !smem_svd
     float* Vg;
     float* Tg;
+    float* Zg;     // scratch C * C
     int m, n, ttype, smem_svd;
     double tau[PMAX];
     Params prm;

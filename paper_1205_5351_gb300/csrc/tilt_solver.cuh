@@ -16,6 +16,7 @@ struct SvdBufs {
     float* B;
     float* V;
     float* T;
+    float* Z;   // global, C * C
 };
 
 __device__ inline unsigned long long clk() { return clock64(); }
@@ -125,12 +126,13 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         // ---- a6: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate)
         t0 = clk();
         const double dM2 = sc->scal[5], M2 = sc->scal[6];
-        const bool warm = haveV && (prm.eps_svd < 0.0 || dM2 < prm.eps_svd * prm.eps_svd * M2);
+        bool warm = haveV && (prm.eps_svd < 0.0 || dM2 < prm.eps_svd * prm.eps_svd * M2);
+        if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
         if (warm) {
             gemm_TV(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
             out.warm++;
         } else {
-            float* t = buf.B; buf.B = buf.T; buf.T = t;
+            for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
             set_identity(buf.V, ldv, Cp);
         }
         const int sw = k2_jacobi(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag);
@@ -145,11 +147,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         const int nk = sc->iscal[1];
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
-        for (int q = threadIdx.x; q < nk * ldb; q += NT) {   // pre-scale kept columns by w_k
-            const int kq = L.kept[q / ldb];
-            buf.B[(size_t)kq * ldb + (q % ldb)] *= L.w[kq];
-        }
-        __syncthreads();
+        svt_left_coeffs(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z);
         {
             float acc[1 + PMAX];
 #pragma unroll
@@ -157,10 +155,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             for (int e = threadIdx.x; e < S; e += NT) {
                 const int r = e % R, c = e / R;
                 float s = 0.f;
-                for (int q = 0; q < nk; ++q) {
-                    const int kq = L.kept[q];
-                    s = fmaf(buf.B[(size_t)kq * ldb + r], buf.V[(size_t)kq * ldv + c], s);
-                }
+                for (int q = 0; q < nk; ++q) s = fmaf(buf.B[(size_t)L.kept[q] * ldb + r], buf.Z[(size_t)q * C + c], s);
                 const float da = s - A[e];
                 acc[0] = fmaf(da, da, acc[0]);
                 A[e] = s;
@@ -322,6 +317,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
         buf.V = pr.pl.Vg;
         buf.T = pr.pl.Tg;
     }
+    buf.Z = pr.pl.Zg;
     // zero the SVD buffers (padding rows/columns are read by the tiled GEMM)
     {
         const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;

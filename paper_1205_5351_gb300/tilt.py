@@ -49,13 +49,14 @@ class Result(ctypes.Structure):
                 ("objective", ctypes.c_double), ("lambda_", ctypes.c_double), ("rank_A", ctypes.c_int),
                 ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("svd_sweeps", ctypes.c_int),
                 ("svd_warm", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("kkt_residual", ctypes.c_double),
-                ("latency_ms", ctypes.c_float)]
+                ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5)]
 
     def to_dict(self) -> dict:
         return dict(status=self.status, p=self.p, tau=np.array(self.tau[: self.p]), objective=self.objective,
                     lam=self.lambda_, rank=self.rank_A, outer_iters=self.outer_iters,
                     inner_iters=self.inner_iters, svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm,
-                    oob=self.oob_pixels, kkt=self.kkt_residual, latency_ms=self.latency_ms)
+                    oob=self.oob_pixels, kkt=self.kkt_residual, latency_ms=self.latency_ms,
+                    phase_cycles=list(self.phase_cycles))
 
 
 class Problem(ctypes.Structure):
@@ -80,6 +81,7 @@ SIGNATURES = {
     "tilt_destroy": (_i, [_vp]),
     "tilt_last_error": (ctypes.c_char_p, [_vp]),
     "tilt_kernel_launches": (ctypes.c_uint64, [_vp]),
+    "tilt_batch_kernel_ms": (_i, [_vp, _P(ctypes.c_float), _i]),
     "tilt_warp_jacobian": (_i, [_vp, _vp, _i, _i, ctypes.c_size_t, _i, _i, _P(_d), _i, _vp, _vp, _P(_d), _P(_i)]),
     "tilt_gram": (_i, [_vp, _vp, _i, _i, _P(_d), _i, _P(_d), _P(_d), _P(_d)]),
     "tilt_svt": (_i, [_vp, _vp, _i, _i, ctypes.c_float, _vp, _P(ctypes.c_float), _P(_i)]),
@@ -182,6 +184,12 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().tilt_kernel_launches(self.h))
+
+    def batch_kernel_ms(self) -> list:
+        """Device time (ms) of each grouped launch of the last submit_batch (CUDA events)."""
+        buf = (ctypes.c_float * 3)()
+        n = _check(lib().tilt_batch_kernel_ms(self.h, buf, 3), self.h)
+        return [float(buf[i]) for i in range(n)]
 
     # ---------------------------------------------------------------- serving API
     def submit(self, img, m: int, n: int, tau0, ttype: int, params: Params | None = None) -> int:
