@@ -201,6 +201,31 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
                float* A_dev, float* E_dev, float* Y_dev, int* iters_out, double* dtau_out,
                double* c1_out, double* c2_out, double* mu_out);
 
+/* ------------------------------------------------------------------------------------------
+ * Allocation-free singular value thresholding.  (The paper has no counterpart: this is a
+ * service of the library, not a step of the method.)
+ *
+ * Same operation and output as tilt_svt, for callers that cannot allocate device memory:
+ * code whose device memory is owned by another memory manager with a fixed budget, and
+ * latency-critical loops in which cudaMalloc / cudaFree would synchronise the device.  It
+ * needs no tilt_ctx and allocates nothing.  Its scratch (the SVD work buffers of matrices
+ * too large for shared memory, the reconstruction coefficients and a status record) is one
+ * file-scope device array of about 772 KiB that every GPU which loads the library holds until the
+ * process exits.
+ *
+ * M_dev (m x n, long-side-contiguous layout as above), A_dev (same layout) and sigma_dev
+ * (min(m, n) floats, may be NULL) are device pointers owned by the caller.  The call is
+ * asynchronous on `stream` (a cudaStream_t; NULL for the legacy default stream): it returns
+ * after the launch, and the outputs are ready when the stream reaches that point.
+ * Limits: 1 <= m, n <= 256, eps >= 0; anything else returns TILT_E_INVAL and launches
+ * nothing.  The first call on a device looks up the scratch array's device address with that
+ * device current and sets the kernel's shared-memory limit; make that first call before any
+ * stream capture.  Every call on a device shares the one scratch array, so calls whose
+ * kernels overlap on the GPU (different streams, or host threads) race and corrupt each
+ * other's results; serialise them on one stream.  Errors: TILT_E_INVAL, TILT_E_CUDA. */
+int tilt_svt_noalloc(const float* M_dev, int m, int n, float eps, float* A_dev, float* sigma_dev,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,10 @@ struct Batch {
 
 }  // namespace
 
+namespace tilt {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace tilt
+
 struct tilt_ctx {
     int device = 0;
     int max_live = 0;

@@ -79,4 +79,7 @@ cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t configure_kernels(size_t max_smem);
 
+// Record an error message for tilt_last_error() on the calling thread; returns code.
+int set_error(int code, const char* msg);
+
 }  // namespace tilt

@@ -87,6 +87,7 @@ SIGNATURES = {
     "tilt_svt": (_i, [_vp, _vp, _i, _i, ctypes.c_float, _vp, _P(ctypes.c_float), _P(_i)]),
     "tilt_inner": (_i, [_vp, _vp, _vp, _i, _i, _P(_d), _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d),
                         _P(_d), _P(_d), _P(_d)]),
+    "tilt_svt_noalloc": (_i, [_vp, _i, _i, ctypes.c_float, _vp, _vp, _vp]),
 }
 
 _lib = None
