@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--patches", type=int, default=1024)
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-outer", type=int, default=None, help="override (small profiling cases only)")
+    ap.add_argument("--max-inner", type=int, default=None, help="override (small profiling cases only)")
     return ap.parse_args()
 
 
@@ -178,10 +180,12 @@ def run_ours(args, rank, world, local_rank, dist):
     items_host = [(p.img, p.m, p.n, p.tau0, p.ttype) for p in patches]
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)
     ctx = tilt.Context(local_rank)
+    over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
+    params = tilt.default_params(**over) if over else None
 
     def step(items, on_device, planes):
         t_sub = time.perf_counter()
-        tickets = ctx.submit_batch(items, on_device=on_device)
+        tickets = ctx.submit_batch(items, params, on_device=on_device)
         pending = dict(enumerate(tickets))
         res = [None] * len(tickets)
         done_at = [0.0] * len(tickets)
@@ -274,6 +278,12 @@ def run_ours(args, rank, world, local_rank, dist):
                                            max(1, sum(sum(r["phase_cycles"]) for r in results)), 4)
                                      for i in range(5)])),
             "kernel_ms": {"sum_of_launches": k_ms, "longest_launch": k_dom},
+            "slowest_patch": (lambda q: {"m": patches[q].m, "n": patches[q].n, "kind": patches[q].meta["kind"],
+                                         "done_ms": lat[q], "outer": results[q]["outer_iters"],
+                                         "inner": results[q]["inner_iters"], "sweeps": results[q]["svd_sweeps"],
+                                         "warm": results[q]["svd_warm"],
+                                         "phase_mcycles": [round(c / 1e6, 2) for c in results[q]["phase_cycles"]]})(
+                int(np.argmax(lat[-len(results):]))),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "kernel": "solver_kernel (fused Algorithm 1, one CTA per patch)",

@@ -204,7 +204,7 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     if (L.smem_svd) {
         L.bg = L.vg = L.tg = 0;
         L.smem = svd + head;
-        L.minb = (L.smem <= 100 * 1024) ? 2 : 1;
+        L.minb = (L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;   // the 2-CTA kernel holds R <= 96 in registers
     } else {
         const size_t nb = (size_t)d.ldb * d.Cp * sizeof(float), nv = (size_t)d.ldv * d.Cp * sizeof(float);
         L.bg = take(nb);

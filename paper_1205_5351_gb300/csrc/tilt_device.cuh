@@ -136,28 +136,61 @@ __device__ inline SmemLayout carve_smem(unsigned char* base) {
 }
 
 // ------------------------------------------------------------------------------ reductions
-// Sum K doubles over the CTA; every thread gets the totals.  Fixed order -> deterministic.
+// Sum K values over the CTA; every thread gets the totals.  Within a warp the partials
+// (FP32 per-thread sums) are added in FP32 by a shuffle tree; the NW warp totals are then
+// added in FP64 by one thread per value (FP64 runs at 1/64 of the FP32 rate on this part, so
+// it is kept to K * NW additions per reduction).  Fixed order -> deterministic.
 template <int K>
 __device__ inline void block_sum(double (&v)[K], double* red) {
-    static_assert(K <= 48, "block_sum staging holds 48 values per warp");
+    static_assert(K <= 44, "block_sum staging: 48 values per warp, the last 44 slots also hold the totals");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float f = (float)v[k];
+        float lo = (float)(v[k] - (double)f);     // keep what FP32 drops of an FP64 partial
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            f += __shfl_xor_sync(0xffffffffu, f, off);
+            lo += __shfl_xor_sync(0xffffffffu, lo, off);
+        }
+        if (lane == 0) red[k * NW + warp] = (double)f + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += red[threadIdx.x * NW + w];
+        red[48 * NW - 1 - threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = red[48 * NW - 1 - k];
+    __syncthreads();
+}
+
+// Exact-order FP64 variant for the once-per-outer-step reductions (norms of the warp, the
+// Gram matrix, the warm-start projections): FP64 shuffle tree in every warp, FP64 sum of the
+// warp totals by one thread per value.
+template <int K>
+__device__ inline void block_sum64(double (&v)[K], double* red) {
+    static_assert(K <= 44, "block_sum staging: 48 values per warp, the last 44 slots also hold the totals");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+        if (lane == 0) red[k * NW + warp] = v[k];
     }
-    if (lane == 0) {
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[k * NW + warp] = v[k];
+        for (int w = 0; w < NW; ++w) s += red[threadIdx.x * NW + w];
+        red[48 * NW - 1 - threadIdx.x] = s;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) s += red[k * NW + w];
-        v[k] = s;
-    }
+    for (int k = 0; k < K; ++k) v[k] = red[48 * NW - 1 - k];
     __syncthreads();
 }
 
@@ -241,21 +274,32 @@ static __device__ void k1_warp_jacobian(const float* __restrict__ img, long long
         const float val = (1.f - fy) * ((1.f - fx) * I00 + fx * I01) + fy * ((1.f - fx) * I10 + fx * I11);
         const float gx = inx ? ((1.f - fy) * (I01 - I00) + fy * (I11 - I10)) : 0.f;
         const float gy = iny ? ((1.f - fx) * (I10 - I00) + fx * (I11 - I01)) : 0.f;
-        double dx[PMAX], dy[PMAX];
-        map_derivs(q, ttype, u, v, dx, dy);
+        // raw Jacobian row: J_k = I_x dx/dtau_k + I_y dy/dtau_k (Sec. 4.1 layout)
+        float jr[PMAX];
+        if (ttype == 8) {
+            const float iu = (float)(u / q.den), iv = (float)(v / q.den), i1 = (float)(1.0 / q.den);
+            const float gxy = gx * (float)q.x + gy * (float)q.y;
+            jr[0] = gx * iu; jr[1] = gx * iv; jr[2] = gx * i1;
+            jr[3] = gy * iu; jr[4] = gy * iv; jr[5] = gy * i1;
+            jr[6] = -gxy * iu; jr[7] = -gxy * iv;
+        } else {
+            const float uf = (float)u, vf = (float)v;
+            jr[0] = gx * uf; jr[1] = gx * vf; jr[2] = gx;
+            jr[3] = gy * uf; jr[4] = gy * vf; jr[5] = gy;
+            jr[6] = 0.f; jr[7] = 0.f;
+        }
         Dhat[e] = val;
         acc[0] += (double)val * (double)val;
         acc[1] += (inx && iny) ? 0.0 : 1.0;
 #pragma unroll
         for (int k = 0; k < PMAX; ++k) {
             if (k < p) {
-                const float jr = gx * (float)dx[k] + gy * (float)dy[k];
-                J[(size_t)k * S + e] = jr;
-                acc[2 + k] += (double)val * (double)jr;
+                J[(size_t)k * S + e] = jr[k];
+                acc[2 + k] += (double)val * (double)jr[k];
             }
         }
     }
-    block_sum<2 + PMAX>(acc, sc->red);
+    block_sum64<2 + PMAX>(acc, sc->red);
     const double s = sqrt(acc[0]);
     if (threadIdx.x == 0) {
         sc->scal[0] = s;
@@ -335,64 +379,78 @@ __device__ inline bool invert_pp(const double* G, double* Gi, int p) {
     return true;
 }
 
-// G = J^T J + Q^T Q, G^-1, J^T D_hat and ||D_hat||^2, d0 = ||W^T W D_hat||_F (FP64).
+// Products accumulated by the Gram pass: index q < 36 is J_a . J_b (a <= b, row-major
+// upper triangle of an 8 x 8), 36 + a is J_a . D_hat, 44 is D_hat . D_hat.
+__device__ inline void gram_index(int q, int& a, int& b) {
+    if (q >= 44) { a = -1; b = -1; return; }
+    if (q >= 36) { a = q - 36; b = -1; return; }
+    int r = 0, rem = q;
+    while (rem >= PMAX - r) { rem -= PMAX - r; ++r; }
+    a = r;
+    b = r + rem;
+}
+
+// G = J^T J + Q^T Q, G^-1, J^T D_hat and ||D_hat||^2, d0 = ||W^T W D_hat||_F (FP64; the
+// 45 products are reduced in three passes of 15 to keep the per-thread accumulators few).
 // Returns false when G is singular.  Results in sc->G, sc->Gi, sc->Q, sc->jd, scal[1] (d0).
 static __device__ bool k5_gram(const Dims& d, int ttype, const double* tau, const float* __restrict__ Dhat,
-                        const float* __restrict__ J, Scratch* sc) {
+                               const float* __restrict__ J, Scratch* sc) {
     const int p = d.p, S = d.S;
-    // pairs (a <= b) then J^T D_hat then ||D_hat||^2
-    constexpr int NPAIR = PMAX * (PMAX + 1) / 2;
-    double acc[NPAIR + PMAX + 1];
+    constexpr int NPROD = 45, CH = 15;
+    double tot[NPROD];
+#pragma unroll 1
+    for (int q0 = 0; q0 < NPROD; q0 += CH) {
+        double acc[CH];
 #pragma unroll
-    for (int k = 0; k < NPAIR + PMAX + 1; ++k) acc[k] = 0.0;
-    for (int e = threadIdx.x; e < S; e += NT) {
-        double jv[PMAX];
+        for (int k = 0; k < CH; ++k) acc[k] = 0.0;
+        for (int e = threadIdx.x; e < S; e += NT) {
+            const double dh = (double)Dhat[e];
 #pragma unroll
-        for (int k = 0; k < PMAX; ++k) jv[k] = (k < p) ? (double)J[(size_t)k * S + e] : 0.0;
-        const double dh = (double)Dhat[e];
-        int q = 0;
+            for (int k = 0; k < CH; ++k) {
+                int a, b;
+                gram_index(q0 + k, a, b);
+                if (a >= p || b >= p) continue;
+                const double va = a < 0 ? dh : (double)J[(size_t)a * S + e];
+                const double vb = b < 0 ? dh : (double)J[(size_t)b * S + e];
+                acc[k] += va * vb;
+            }
+        }
+        block_sum64<CH>(acc, sc->red);
 #pragma unroll
-        for (int a = 0; a < PMAX; ++a)
-#pragma unroll
-            for (int b = a; b < PMAX; ++b) acc[q++] += jv[a] * jv[b];
-#pragma unroll
-        for (int a = 0; a < PMAX; ++a) acc[NPAIR + a] += jv[a] * dh;
-        acc[NPAIR + PMAX] += dh * dh;
+        for (int k = 0; k < CH; ++k) tot[q0 + k] = acc[k];
     }
-    block_sum<NPAIR + PMAX + 1>(acc, sc->red);
     __shared__ int ok_s;
     if (threadIdx.x == 0) {
         constraint_rows(tau, ttype, d.m, d.n, p, sc->Q);
-        int q = 0;
-        for (int a = 0; a < PMAX; ++a)
-            for (int b = a; b < PMAX; ++b) {
-                double g = acc[q++];
-                if (a < p && b < p) {
-                    for (int l = 0; l < 3; ++l) g += sc->Q[l * PMAX + a] * sc->Q[l * PMAX + b];
-                    sc->G[a * PMAX + b] = g;
-                    sc->G[b * PMAX + a] = g;
-                }
+        double JJ[PMAX][PMAX];
+        for (int q = 0; q < 36; ++q) {
+            int a, b;
+            gram_index(q, a, b);
+            if (a < p && b < p) { JJ[a][b] = tot[q]; JJ[b][a] = tot[q]; }
+        }
+        for (int a = 0; a < p; ++a)
+            for (int b = 0; b < p; ++b) {
+                double g = JJ[a][b];
+                for (int l = 0; l < 3; ++l) g += sc->Q[l * PMAX + a] * sc->Q[l * PMAX + b];
+                sc->G[a * PMAX + b] = g;
             }
-        for (int a = 0; a < p; ++a) sc->jd[a] = acc[NPAIR + a];
+        for (int a = 0; a < p; ++a) sc->jd[a] = tot[36 + a];
         const bool ok = invert_pp(sc->G, sc->Gi, p);
         ok_s = ok ? 1 : 0;
         // ||W^T W D||^2 = ||D||^2 - 2 jd^T c + c^T (J^T J) c with c = G^-1 jd
         double c[PMAX];
         for (int a = 0; a < p; ++a) {
-            double s = 0;
-            for (int b = 0; b < p; ++b) s += sc->Gi[a * PMAX + b] * sc->jd[b];
-            c[a] = s;
+            double v = 0;
+            for (int b = 0; b < p; ++b) v += sc->Gi[a * PMAX + b] * sc->jd[b];
+            c[a] = v;
         }
-        double q2 = acc[NPAIR + PMAX];
-        int qq = 0;
-        for (int a = 0; a < PMAX; ++a)
-            for (int b = a; b < PMAX; ++b) {
-                const double jj = acc[qq++];
-                if (a < p && b < p) q2 += (a == b ? 1.0 : 2.0) * c[a] * c[b] * jj;
-            }
-        for (int a = 0; a < p; ++a) q2 -= 2.0 * sc->jd[a] * c[a];
+        double q2 = tot[44];
+        for (int a = 0; a < p; ++a) {
+            q2 -= 2.0 * sc->jd[a] * c[a];
+            for (int b = 0; b < p; ++b) q2 += c[a] * c[b] * JJ[a][b];
+        }
         sc->scal[1] = sqrt(fmax(q2, 0.0));
-        sc->scal[2] = acc[NPAIR + PMAX];
+        sc->scal[2] = tot[44];
     }
     __syncthreads();
     const bool ok = ok_s != 0;
@@ -455,73 +513,181 @@ static __device__ double spectral_norm(const float* __restrict__ X, const Dims& 
 }
 
 // ------------------------------------------------------------------------------ K2: SVD
-// One-sided (Hestenes) Jacobi on the columns of B (R x C, column stride ldb), accumulating
-// the rotations into V (C x C, stride ldv).  Round-robin ordering: every round is a set of
-// disjoint column pairs, one pair per warp at a time, rows spread over the lanes; the
-// three dot products of a pair are reduced with warp shuffles.  A pair is rotated when
-// |b_i . b_j| > tol ||b_i|| ||b_j||; the sweeps stop when a sweep rotates nothing.
-// Returns the number of sweeps.
+// One-sided (Hestenes) Jacobi on the columns of B (R x C, column stride ldb, a multiple of
+// 4), accumulating the rotations into V (C x C, stride ldv, a multiple of 4).
+//
+// Round-robin ordering: each round is a set of disjoint column pairs.  A pair is handled by
+// a group of 8 lanes (4 pairs in flight per warp, 64 per CTA): lane g holds the float4
+// chunks g, g+8, g+16, ... of both columns, so the three dot products need 3 shuffle levels
+// and, when the columns fit in registers (R <= 128), the rotation reuses the loaded values.
+// A pair is rotated when |b_i.b_j| > tol ||b_i|| ||b_j||, in Rutishauser's form
+// x' = x - s (y + r x), y' = y + s (x - r y), r = tan(theta/2), so that small angles do not
+// inflate the column norms (with c rounded to 1 the plain form grows them by t^2/2 per
+// rotation).  Sweeps stop when one rotates nothing, or when the largest rotated cosine is
+// below 32 tol (cyclic Jacobi converges quadratically near the end, so the next sweep would
+// find nothing above tol).  Returns the number of sweeps.
+struct RotParams {
+    float s, r;
+    bool rot;
+    float cosabs;
+};
+
+__device__ inline RotParams rotation_for(float a, float b, float g, float tol) {
+    // rotate when |g| > tol sqrt(a b), tested as g^2 > tol^2 a b (no square roots);
+    // tan(theta) = t = 2g / (d + sgn(d) sqrt(d^2 + 4 g^2)), d = b - a (the smaller root);
+    // with q = sqrt(1 + t^2): s = sin(theta) = t / q, r = tan(theta/2) = t / (1 + q)
+    RotParams p;
+    const float ab = a * b;
+    p.rot = (ab > 0.f) && (g * g > tol * tol * ab);
+    p.cosabs = 0.f;
+    p.s = 0.f;
+    p.r = 0.f;
+    if (p.rot) {
+        p.cosabs = fabsf(g) * rsqrtf(ab);
+        const float d = b - a;
+        const float w = 2.f * g;
+        const float h = sqrtf(fmaf(d, d, w * w));
+        const float t = __fdividef(w, d + copysignf(h, d));
+        const float q = sqrtf(fmaf(t, t, 1.f));
+        p.s = __fdividef(t, q);
+        p.r = __fdividef(t, 1.f + q);
+    }
+    return p;
+}
+
+__device__ inline float4 rot_x(float4 x, float4 y, float s, float r) {
+    return make_float4(x.x - s * fmaf(r, x.x, y.x), x.y - s * fmaf(r, x.y, y.y), x.z - s * fmaf(r, x.z, y.z),
+                       x.w - s * fmaf(r, x.w, y.w));
+}
+__device__ inline float4 rot_y(float4 x, float4 y, float s, float r) {
+    return make_float4(y.x + s * fmaf(-r, y.x, x.x), y.y + s * fmaf(-r, y.y, x.y), y.z + s * fmaf(-r, y.z, x.z),
+                       y.w + s * fmaf(-r, y.w, x.w));
+}
+
+__device__ inline float group8_sum(float v, unsigned mask) {
+    v += __shfl_xor_sync(mask, v, 1, 8);
+    v += __shfl_xor_sync(mask, v, 2, 8);
+    v += __shfl_xor_sync(mask, v, 4, 8);
+    return v;
+}
+
+// Rotate the V columns i, j (C rows in float4 chunks, nqv chunks).
+__device__ inline void rotate_v(float* V, int ldv, int i, int j, int nqv, int g, float s, float r) {
+    float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
+    float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
+    for (int q = g; q < nqv; q += 8) {
+        const float4 x = vi[q], y = vj[q];
+        vi[q] = rot_x(x, y, s, r);
+        vj[q] = rot_y(x, y, s, r);
+    }
+}
+
+template <int NCH>
 static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                         int* flag) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                                int* flag) {
+    if (C < 2) return 0;
+    const int lane = threadIdx.x & 31;
+    const int grp = threadIdx.x >> 3, g = lane & 7;
+    constexpr int NG = NT / 8;
+    const unsigned gmask = 0xFFu << (lane & 24);
     const int Ce = C + (C & 1);
     const int npairs = Ce / 2;
-    const int nrounds = Ce - 1;
+    const int nr = Ce - 1;
+    const int nqb = ldb / 4, nqv = ldv / 4;
+    const bool in_regs = nqb <= 8 * NCH;     // R <= 32 NCH: NCH chunks per lane hold a column
+    float* fl = reinterpret_cast<float*>(flag);
     int sweep = 0;
-    if (C < 2) return 0;
     while (sweep < max_sweeps) {
-        if (threadIdx.x == 0) flag[sweep & 1] = 0;
+        if (threadIdx.x == 0) { flag[0] = 0; fl[1] = 0.f; }
         __syncthreads();
         bool rotated = false;
-        for (int round = 0; round < nrounds; ++round) {
-            for (int k = warp; k < npairs; k += NW) {
-                const int i = (k == 0) ? 0 : 1 + (k - 1 + round) % nrounds;
-                const int j = 1 + (Ce - 2 - k + round) % nrounds;
+        float maxcos = 0.f;
+        for (int round = 0; round < nr; ++round) {
+            for (int k = grp; k < npairs; k += NG) {
+                int i = 0;
+                if (k) { i = k - 1 + round; if (i >= nr) i -= nr; i += 1; }
+                int j = Ce - 2 - k + round;
+                if (j >= nr) j -= nr;
+                j += 1;
                 if (i >= C || j >= C) continue;
-                float* bi = B + (size_t)i * ldb;
-                float* bj = B + (size_t)j * ldb;
-                float a = 0.f, b = 0.f, g = 0.f;
-                for (int r = lane; r < R; r += 32) {
-                    const float x = bi[r], y = bj[r];
-                    a = fmaf(x, x, a);
-                    b = fmaf(y, y, b);
-                    g = fmaf(x, y, g);
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                g = warp_sum(g);
-                if (fabsf(g) > tol * sqrtf(a) * sqrtf(b)) {
-                    // rotation angle from the 2 x 2 Gram matrix [[a, g], [g, b]]; applied in
-                    // Rutishauser's form x' = x - s (y + r x), y' = y + s (x - r y) with
-                    // r = tan(theta/2), so that small angles do not inflate the column norms
-                    // (with c rounded to 1 the plain form grows them by t^2/2 per rotation)
-                    const float zeta = (b - a) / (2.f * g);
-                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                    const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
-                    const float s = c * t;
-                    const float rr = s / (1.f + c);
-                    for (int r = lane; r < R; r += 32) {
-                        const float x = bi[r], y = bj[r];
-                        bi[r] = x - s * fmaf(rr, x, y);
-                        bj[r] = y + s * fmaf(-rr, y, x);
+                float4* bi = reinterpret_cast<float4*>(B + (size_t)i * ldb);
+                float4* bj = reinterpret_cast<float4*>(B + (size_t)j * ldb);
+                float a = 0.f, b = 0.f, gg = 0.f;
+                if (in_regs) {
+                    float4 x[NCH], y[NCH];
+                    float pa[NCH], pb[NCH], pg[NCH];
+#pragma unroll
+                    for (int t = 0; t < NCH; ++t) {
+                        const int q = g + 8 * t;
+                        if (q < nqb) {
+                            x[t] = bi[q];
+                            y[t] = bj[q];
+                        } else {
+                            x[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            y[t] = x[t];
+                        }
+                        pa[t] = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, x[t].w * x[t].w)));
+                        pb[t] = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, y[t].w * y[t].w)));
+                        pg[t] = fmaf(x[t].x, y[t].x, fmaf(x[t].y, y[t].y, fmaf(x[t].z, y[t].z, x[t].w * y[t].w)));
                     }
-                    float* vi = V + (size_t)i * ldv;
-                    float* vj = V + (size_t)j * ldv;
-                    for (int r = lane; r < C; r += 32) {
-                        const float x = vi[r], y = vj[r];
-                        vi[r] = x - s * fmaf(rr, x, y);
-                        vj[r] = y + s * fmaf(-rr, y, x);
+#pragma unroll
+                    for (int t = 0; t < NCH; ++t) {
+                        a += pa[t];
+                        b += pb[t];
+                        gg += pg[t];
                     }
-                    rotated = true;
+                    a = group8_sum(a, gmask);
+                    b = group8_sum(b, gmask);
+                    gg = group8_sum(gg, gmask);
+                    const RotParams rp = rotation_for(a, b, gg, tol);
+                    if (rp.rot) {
+#pragma unroll
+                        for (int t = 0; t < NCH; ++t) {
+                            const int q = g + 8 * t;
+                            if (q < nqb) {
+                                bi[q] = rot_x(x[t], y[t], rp.s, rp.r);
+                                bj[q] = rot_y(x[t], y[t], rp.s, rp.r);
+                            }
+                        }
+                        rotate_v(V, ldv, i, j, nqv, g, rp.s, rp.r);
+                        rotated = true;
+                        maxcos = fmaxf(maxcos, rp.cosabs);
+                    }
+                } else {
+                    for (int q = g; q < nqb; q += 8) {
+                        const float4 x = bi[q], y = bj[q];
+                        a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
+                        b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
+                        gg = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, gg))));
+                    }
+                    a = group8_sum(a, gmask);
+                    b = group8_sum(b, gmask);
+                    gg = group8_sum(gg, gmask);
+                    const RotParams rp = rotation_for(a, b, gg, tol);
+                    if (rp.rot) {
+                        for (int q = g; q < nqb; q += 8) {
+                            const float4 x = bi[q], y = bj[q];
+                            bi[q] = rot_x(x, y, rp.s, rp.r);
+                            bj[q] = rot_y(x, y, rp.s, rp.r);
+                        }
+                        rotate_v(V, ldv, i, j, nqv, g, rp.s, rp.r);
+                        rotated = true;
+                        maxcos = fmaxf(maxcos, rp.cosabs);
+                    }
                 }
             }
             __syncthreads();
         }
-        if (rotated) flag[sweep & 1] = 1;
+        if (rotated) {
+            flag[0] = 1;
+            atomicMax(reinterpret_cast<int*>(&fl[1]), __float_as_int(maxcos));   // non-negative floats order as ints
+        }
         __syncthreads();
-        const int any = flag[sweep & 1];
+        const int any = flag[0];
+        const float mc = fl[1];
+        __syncthreads();
         ++sweep;
-        if (!any) break;
+        if (!any || mc * mc < tol) break;
     }
     return sweep;
 }
@@ -576,16 +742,30 @@ static __device__ void svt_weights(const float* B, int ldb, int R, int C, float 
 static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb, int R,
                                        int C, const float* sigma, const float* w, const int* kept, int nk,
                                        float* __restrict__ Z) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int idx = warp; idx < nk * C; idx += NW) {
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 3, g = lane & 7;
+    const unsigned gmask = 0xFFu << (lane & 24);
+    constexpr int NG = NT / 8;
+    const bool vec = ((ldx & 3) == 0) && ((ldb & 3) == 0);
+    for (int idx = grp; idx < nk * C; idx += NG) {
         const int q = idx / C, c = idx - q * C;
         const int k = kept[q];
         const float* x = X + (size_t)c * ldx;
         const float* b = B + (size_t)k * ldb;
         float s = 0.f;
-        for (int r = lane; r < R; r += 32) s = fmaf(x[r], b[r], s);
-        s = warp_sum(s);
-        if (lane == 0) {
+        if (vec) {
+            const int nq = (R + 3) >> 2;   // padding rows of B are zero, X rows beyond R exist (ldx >= R rounded)
+            for (int t = g; t < nq; t += 8) {
+                const float4 xv = reinterpret_cast<const float4*>(x)[t];
+                const float4 bv = reinterpret_cast<const float4*>(b)[t];
+                s = fmaf(xv.x, bv.x, fmaf(xv.y, bv.y, fmaf(xv.z, bv.z, fmaf(xv.w, bv.w, s))));
+            }
+        } else {
+            for (int r = g; r < R; r += 8) s = fmaf(x[r], b[r], s);
+        }
+        s += __shfl_xor_sync(gmask, s, 1, 8);
+        s += __shfl_xor_sync(gmask, s, 2, 8);
+        s += __shfl_xor_sync(gmask, s, 4, 8);
+        if (g == 0) {
             const float sg = sigma[k];
             Z[(size_t)q * C + c] = s * (w[k] / (sg * sg));
         }

@@ -16,14 +16,16 @@ __device__ inline void copy_to_shared(T* dst, const T* src) {
 
 // One CTA per problem: the whole of Algorithm 1.  The result record and the completion
 // flag live in host-mapped memory, so the host sees every problem retire on its own.
-template <int MINB>
+// MINB CTAs per SM; NCH float4 chunks per lane keep a Jacobi column pair in registers
+// (R <= 32 NCH), fewer for the 2-CTA variant so that it fits 64 registers per thread.
+template <int MINB, int NCH>
 __global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const int* order) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     __shared__ Problem sp;
     __shared__ Result sres;
     SmemLayout L = carve_smem(smem_raw);
     copy_to_shared(&sp, probs + order[blockIdx.x]);
-    solve_problem(sp, L, sres);
+    solve_problem<NCH>(sp, L, sres);
     if (threadIdx.x == 0) {
         *sp.res = sres;
         __threadfence_system();
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     }
     __syncthreads();
     set_identity(V, d.ldv, d.Cp);
-    const int sw = k2_jacobi(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag);
+    const int sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag);
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
     svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg);
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     __shared__ Result cyc;
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
-    InnerOut io = k_inner(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc);
+    InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc);
     if (threadIdx.x == 0) {
         a.out->status = io.bad ? -1 : 0;
         a.out->iters = io.iters;
@@ -136,9 +138,9 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
 
 cudaError_t configure_kernels(size_t max_smem) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(solver_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    if ((e = cudaFuncSetAttribute(solver_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
-    if ((e = cudaFuncSetAttribute(solver_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    if ((e = cudaFuncSetAttribute(solver_kernel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
     if ((e = cudaFuncSetAttribute(svt_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
@@ -150,9 +152,9 @@ cudaError_t configure_kernels(size_t max_smem) {
 cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (minb >= 2)
-        solver_kernel<2><<<count, NT, smem, st>>>(probs, order);
+        solver_kernel<2, 3><<<count, NT, smem, st>>>(probs, order);
     else
-        solver_kernel<1><<<count, NT, smem, st>>>(probs, order);
+        solver_kernel<1, 4><<<count, NT, smem, st>>>(probs, order);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ __device__ inline float soft(float x, float eps) {
 //   stop when c1 < eps1 and c2 < eps2; mu <- min(mu_max, rho mu)
 // W^T W v = v - J (G^-1 (J^T v)); the J^T products of A' and E' are accumulated while
 // those planes are produced, so every W^T W costs one extra pass only.
+template <int NCH>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
@@ -54,22 +55,25 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
 
     // ---- prologue: J^T A, J^T E, J^T Y; project Y (Eq. Y_new_warmstart); P_0; M_0
     {
-        double acc[3 * PMAX];
+        float facc[3 * PMAX];
 #pragma unroll
-        for (int k = 0; k < 3 * PMAX; ++k) acc[k] = 0.0;
+        for (int k = 0; k < 3 * PMAX; ++k) facc[k] = 0.f;
         for (int e = threadIdx.x; e < S; e += NT) {
             const float a = A[e], ee = E[e], y = Y[e];
 #pragma unroll
             for (int k = 0; k < PMAX; ++k) {
                 if (k < p) {
                     const float jk = J[(size_t)k * S + e];
-                    acc[k] += (double)(jk * a);
-                    acc[PMAX + k] += (double)(jk * ee);
-                    acc[2 * PMAX + k] += (double)(jk * y);
+                    facc[k] = fmaf(jk, a, facc[k]);
+                    facc[PMAX + k] = fmaf(jk, ee, facc[PMAX + k]);
+                    facc[2 * PMAX + k] = fmaf(jk, y, facc[2 * PMAX + k]);
                 }
             }
         }
-        block_sum<3 * PMAX>(acc, sc->red);
+        double acc[3 * PMAX];
+#pragma unroll
+        for (int k = 0; k < 3 * PMAX; ++k) acc[k] = facc[k];
+        block_sum64<3 * PMAX>(acc, sc->red);
         if (threadIdx.x == 0) {
             double v[PMAX];
             for (int k = 0; k < p; ++k) {
@@ -113,11 +117,11 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             g[1] += (double)(mv * mv);
             Mp[e] = mv;
         }
-        block_sum<2>(g, sc->red);
+        block_sum64<2>(g, sc->red);
         if (threadIdx.x == 0) { sc->scal[5] = g[0]; sc->scal[6] = g[1]; }
         __syncthreads();
     }
-    cyc->cyc_elem += clk() - t0;
+    if (threadIdx.x == 0) cyc->cyc_elem += clk() - t0;
 
     const double d0 = sc->scal[1] > 0.0 ? sc->scal[1] : 1.0;
     double mu = mu0;
@@ -135,13 +139,13 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
             set_identity(buf.V, ldv, Cp);
         }
-        const int sw = k2_jacobi(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag);
+        const int sw = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag);
         haveV = true;
         out.sweeps += sw;
         const float eps = (float)(1.0 / mu);
         svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
         unsigned long long t1 = clk();
-        cyc->cyc_svd += t1 - t0;
+        if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
 
         // ---- a7: A' = sum_kept w_k b_k v_k^T; ||A' - A||^2; J^T A'
         const int nk = sc->iscal[1];
@@ -152,16 +156,32 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             float acc[1 + PMAX];
 #pragma unroll
             for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
-            for (int e = threadIdx.x; e < S; e += NT) {
-                const int r = e % R, c = e / R;
-                float s = 0.f;
-                for (int q = 0; q < nk; ++q) s = fmaf(buf.B[(size_t)L.kept[q] * ldb + r], buf.Z[(size_t)q * C + c], s);
-                const float da = s - A[e];
-                acc[0] = fmaf(da, da, acc[0]);
-                A[e] = s;
+            // four consecutive rows of one column per thread: float4 reads of B
+            const int nq = (R + 3) >> 2;
+            for (int idx = threadIdx.x; idx < nq * C; idx += NT) {
+                const int c = idx / nq, r0 = (idx - c * nq) * 4;
+                float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < nk; ++q) {
+                    const float4 b4 = *reinterpret_cast<const float4*>(buf.B + (size_t)L.kept[q] * ldb + r0);
+                    const float z = buf.Z[(size_t)q * C + c];
+                    s4.x = fmaf(b4.x, z, s4.x);
+                    s4.y = fmaf(b4.y, z, s4.y);
+                    s4.z = fmaf(b4.z, z, s4.z);
+                    s4.w = fmaf(b4.w, z, s4.w);
+                }
+                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                for (int k2 = 0; k2 < PMAX; ++k2)
-                    if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], s, acc[1 + k2]);
+                for (int u = 0; u < 4; ++u) {
+                    if (r0 + u >= R) break;
+                    const int e = c * R + r0 + u;
+                    const float sa = sv[u];
+                    const float da = sa - A[e];
+                    acc[0] = fmaf(da, da, acc[0]);
+                    A[e] = sa;
+#pragma unroll
+                    for (int k2 = 0; k2 < PMAX; ++k2)
+                        if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+                }
             }
             double dacc[1 + PMAX];
 #pragma unroll
@@ -179,7 +199,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             __syncthreads();
         }
         unsigned long long t2 = clk();
-        cyc->cyc_recon += t2 - t1;
+        if (threadIdx.x == 0) cyc->cyc_recon += t2 - t1;
 
         // ---- a8: E' = T_{lam/mu}(E - Y/mu - W^T W (A' + E - D_hat)); ||E' - E||^2; J^T E'; ||E'||_1
         const float imu = (float)(1.0 / mu);
@@ -268,7 +288,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             }
             __syncthreads();
         }
-        cyc->cyc_elem += clk() - t2;
+        if (threadIdx.x == 0) cyc->cyc_elem += clk() - t2;
         const double c1 = sqrt(sc->scal[10]) / d0;
         out.c1 = c1;
         out.c2 = c2;
@@ -302,6 +322,7 @@ __device__ inline double corner_shift(const double* tau, const double* dtau, int
 }
 
 // Algorithm 1 for one problem.
+template <int NCH>
 static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Result& res) {
     Scratch* sc = L.sc;
     const Dims d = make_dims(pr.m, pr.n, pr.p);
@@ -337,7 +358,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
 
     unsigned long long t0 = clk();
     k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
-    res.cyc_warp += clk() - t0;
+    if (threadIdx.x == 0) res.cyc_warp += clk() - t0;
     if (!(sc->scal[0] > 0.0)) {
         status = -3;
     } else {
@@ -355,12 +376,12 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
                 if (!(sc->scal[0] > 0.0)) { status = -3; break; }
             }
             unsigned long long t1 = clk();
-            res.cyc_warp += t1 - t0;
+            if (threadIdx.x == 0) res.cyc_warp += t1 - t0;
             if (!k5_gram(d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc)) { status = -2; break; }
             double mu0 = prm.mu0;
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
-            res.cyc_other += clk() - t1;
-            InnerOut io = k_inner(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
+            if (threadIdx.x == 0) res.cyc_other += clk() - t1;
+            InnerOut io = k_inner<NCH>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
                                   pr.pl.Mp, buf, haveV, L, &res);
             inner_total += io.iters;
             sweeps += io.sweeps;
