@@ -29,6 +29,31 @@ sys.path.insert(0, ROOT)
 METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
 WORKLOAD = ("1024 affine (p=6) patches, sides uniform 40-120 (non-square), rank 1-5 textures or "
             "checkerboards of period 4-16, rotation +-30 deg, skew +-0.2, corruption 0-10 %")
+
+# Other configurations (parity-test cases; measurable with --workload):
+WORKLOADS = {
+    "affine": (WORKLOAD, 1024, {}),
+    "small": ("one 50x50 affine patch, rank-3 texture, rotation 20 deg, skew 0.15, 5 % corruption, "
+              "lambda = 1/sqrt(50), inner tolerance 1e-7", 1, {"eps1": 1e-7}),
+    "projective": ("256 projective (p=8) patches 200x200, rank-4 texture + N(0, 0.01^2) noise, rotation "
+                   "+-25 deg, skew +-0.2, perspective +-1e-3, 10 % corruption", 256, {}),
+    "multistart": ("64 projective 512x512 patches, rank-5 texture, 10 % corruption, 9 starts each "
+                   "(initial rotations -40..40 deg), lowest objective kept", 576, {}),
+}
+
+
+def make_patches(workload, count, first):
+    from paper_1205_5351_gb300 import synth
+    if workload == "affine":
+        return synth.mixed_affine_batch(count, first=first)
+    if workload == "small":
+        return [synth.small_affine(first + i) for i in range(count)]
+    if workload == "projective":
+        return synth.projective_batch(count, first=first)
+    if workload == "multistart":
+        groups = max(1, count // len(synth.MULTISTART_ANGLES))
+        return synth.multistart_batch(groups, first=first // len(synth.MULTISTART_ANGLES))
+    raise ValueError(workload)
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
@@ -40,9 +65,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--patches", type=int, default=1024)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream"], default="affine")
+    ap.add_argument("--patches", type=int, default=None, help="patches per GPU (default: the workload's)")
+    ap.add_argument("--plain-seconds", type=float, default=15.0, help="budget of the plain GPU solver sample")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stream-seconds", type=float, default=600.0, help="wall-clock cap of the served stream")
     ap.add_argument("--max-outer", type=int, default=None, help="override (small profiling cases only)")
     ap.add_argument("--max-inner", type=int, default=None, help="override (small profiling cases only)")
     return ap.parse_args()
@@ -52,11 +80,10 @@ def parse_args():
 def _oracle_one(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import tilt_oracle as O
-    from paper_1205_5351_gb300 import synth
-    idx, first = args
-    p = synth.mixed_affine_batch(1, first=first + idx)[0]
+    idx, first, workload = args
+    p = make_patches(workload, 1, first + idx)[0]
     t0 = time.perf_counter()
-    r = O.tilt(p.img.astype("float64"), p.tau0, p.ttype, p.m, p.n, O.Params())
+    r = O.tilt(p.img.astype("float64"), p.tau0, p.ttype, p.m, p.n, O.Params(**WORKLOADS[workload][2]))
     return idx, time.perf_counter() - t0, r.tau.tolist(), r.inner_iters, r.rank
 
 
@@ -69,7 +96,7 @@ def cpu_pool():
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None):
+def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload="affine"):
     """Oracle on patches first, first+1, ... until about budget_s of wall time is spent."""
     max_patches = max_patches or 4 * cores
     t0 = time.perf_counter()
@@ -77,7 +104,7 @@ def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None):
     nxt = 0
     while nxt < max_patches and (time.perf_counter() - t0) < budget_s:
         batch = list(range(nxt, min(nxt + cores, max_patches)))
-        out += pool.map(_oracle_one, [(i, first) for i in batch])
+        out += pool.map(_oracle_one, [(i, first, workload) for i in batch])
         nxt = batch[-1] + 1
     wall = time.perf_counter() - t0
     return out, wall
@@ -168,20 +195,24 @@ def run_ours(args, rank, world, local_rank, dist):
 
     from paper_1205_5351_gb300 import synth, tilt
 
+    desc, default_n, wl_params = WORKLOADS[args.workload]
+    args.patches = args.patches or default_n
     pool = cores = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    oracle_ok = args.workload != "multistart"     # the FP64 oracle needs ~15 min per 512^2 solve
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and oracle_ok:
         pool, cores = cpu_pool()          # before any CUDA call
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    first = rank * args.patches
-    patches = synth.mixed_affine_batch(args.patches, first=first)
+    from paper_1205_5351_gb300 import multigpu
+    first = multigpu.first_index(args.patches, rank)
+    patches = make_patches(args.workload, args.patches, first)
     imgs = [torch.from_numpy(p.img).to(dev) for p in patches]
     items_dev = [(im, p.m, p.n, p.tau0, p.ttype) for im, p in zip(imgs, patches)]
     items_host = [(p.img, p.m, p.n, p.tau0, p.ttype) for p in patches]
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)
     ctx = tilt.Context(local_rank)
     over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
-    params = tilt.default_params(**over) if over else None
+    params = tilt.default_params(**{**wl_params, **over})
 
     def step(items, on_device, planes):
         t_sub = time.perf_counter()
@@ -204,6 +235,10 @@ def run_ours(args, rank, world, local_rank, dist):
         if dist:
             dist.barrier()
 
+    # autotune the Jacobi group width for every size bucket of the workload (untimed)
+    t_tune = time.perf_counter()
+    ctx.autotune(sorted({(p.m, p.n) for p in patches}), patches[0].ttype)
+    tune_s = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         step(items_dev, True, False)
     # ---- timed: device-resident inputs
@@ -235,10 +270,10 @@ def run_ours(args, rank, world, local_rank, dist):
         step(items_host, False, True)
         e2e_times.append(1e3 * (time.perf_counter() - t0))
 
+    from paper_1205_5351_gb300 import multigpu
     ms = statistics.mean(times)
-    tot = torch.tensor([max(times), max(e2e_times)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    # max over ranks of the timed regions (each rank solved its own batch: weak scaling)
+    tot = multigpu.max_over_ranks([max(times), max(e2e_times)], dist, dev)
     n_total = args.patches * world
     inner = sum(r["inner_iters"] for r in results)
     out = None
@@ -263,7 +298,7 @@ def run_ours(args, rank, world, local_rank, dist):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "patches_per_gpu": args.patches, "p": 6,
+            "config": {"workload": desc, "patches_per_gpu": len(patches), "p": patches[0].ttype,
                        "l2": "512 MiB written before every step; inputs exceed L2"},
             "ladmap_iters_per_s": inner * world / (max(times) * 1e-3),
             "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
@@ -289,13 +324,34 @@ def run_ours(args, rank, world, local_rank, dist):
                          "kernel": "solver_kernel (fused Algorithm 1, one CTA per patch)",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA issue rate)"},
             "gpu_launches": launches // max(1, args.steps),
+            "autotune_s": round(tune_s, 2),
             "clocks": clk,
             "e2e": {"value": n_total / (float(tot[1]) * 1e-3), "unit": "patches/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
         value = n_total / (float(tot[0]) * 1e-3)
+        if args.workload == "multistart":
+            starts = len(synth.MULTISTART_ANGLES)
+            best = tilt.best_of(results, starts)
+            out["multistart"] = {"groups": len(best), "starts": starts,
+                                 "chosen_start_histogram": {str(b): best.count(b) for b in sorted(set(best))}}
+        if args.plain_seconds > 0 and args.workload in ("affine", "small", "projective"):
+            from baseline.plain_gpu import tilt_plain
+            t0 = time.perf_counter()
+            k = 0
+            while k < len(patches) and time.perf_counter() - t0 < args.plain_seconds:
+                p = patches[k]
+                tilt_plain(imgs[k], p.tau0, p.ttype, p.m, p.n, **{kk: vv for kk, vv in wl_params.items()})
+                torch.cuda.synchronize()
+                k += 1
+            plain = k / (time.perf_counter() - t0)
+            out["plain_gpu"] = {"value": plain, "unit": "patches/s",
+                                "sample": f"first {k} patches, one at a time (PyTorch ops, cuSOLVER SVD "
+                                          "per inner iteration, host-side stopping test)"}
+            out["speedup_vs_plain_gpu"] = value / plain if plain > 0 else None
         if pool is not None:
-            sample, wall = run_oracle_sample(pool, cores, args.cpu_seconds, first=first)
+            sample, wall = run_oracle_sample(pool, cores, args.cpu_seconds, first=first,
+                                             max_patches=min(4 * cores, len(patches)), workload=args.workload)
             pool.close()
             errs = []
             for idx, secs, tau, iters, rk in sample:
@@ -303,7 +359,7 @@ def run_ours(args, rank, world, local_rank, dist):
                 errs.append(float(np.linalg.norm(t - np.asarray(tau)) / np.linalg.norm(tau)))
             ok = sum(1 for e in errs if e <= 1e-3)
             frac = ok / len(errs) if errs else None
-            out["cpu_baseline"] = {"value": len(sample) / wall, "unit": "patches/s", "cores": cores,
+            out["cpu_baseline"] = {"value": len(sample) / wall if sample else None, "unit": "patches/s", "cores": cores,
                                    "kind": "oracle", "cpu": cpu_model(),
                                    "sample": f"first {len(sample)} patches of the same workload, "
                                              f"one per process, {wall:.1f} s wall"}
@@ -315,19 +371,83 @@ def run_ours(args, rank, world, local_rank, dist):
     return out
 
 
+# ----------------------------------------------------------------------------- served stream
+def run_stream(args, rank, world, local_rank):
+    """Poisson arrivals (2000/s) of patches with sides 32..256, half affine / half projective,
+    submitted one by one from host memory as they arrive and polled to completion; reports
+    throughput and submit-to-completion latency percentiles."""
+    import torch
+
+    from paper_1205_5351_gb300 import synth, tilt
+
+    torch.cuda.set_device(local_rank)
+    n = args.patches or 2000
+    times, patches = synth.served_stream(n, first=rank * n)
+    over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
+    params = tilt.default_params(**over)
+    ctx = tilt.Context(local_rank)
+    warm = synth.served_stream(4, first=10**5)[1]
+    for p in warm:
+        ctx.wait(ctx.submit(p.img, p.m, p.n, p.tau0, p.ttype, params), 600000)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = ctx.launches
+    pending = {}
+    lat = []
+    inner = 0
+    submitted = 0
+    t0 = time.perf_counter()
+    deadline = t0 + args.stream_seconds
+    while len(lat) < n and time.perf_counter() < deadline:
+        now = time.perf_counter() - t0
+        while submitted < n and times[submitted] <= now:
+            p = patches[submitted]
+            pending[ctx.submit(p.img, p.m, p.n, p.tau0, p.ttype, params)] = times[submitted]
+            submitted += 1
+        progressed = False
+        for t in list(pending):
+            r = ctx.poll(t)
+            if r is not None:
+                lat.append(1e3 * ((time.perf_counter() - t0) - pending.pop(t)))
+                inner += r["inner_iters"]
+                progressed = True
+        if not progressed:
+            time.sleep(50e-6)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = ctx.launches - launches0
+    try:
+        ctx.close()
+    except tilt.TiltError as e:     # problems still running at the cap: reported, not awaited
+        print(f"context close: {e}", file=sys.stderr)
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": len(lat) / wall, "unit": "patches/s", "n_gpus": world, "steps": 1,
+            "warmup": len(warm), "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served stream: Poisson arrivals at 2000/s, sides uniform 32-256, half affine / "
+                                   "half projective, rank 1-6, corruption 0-15 %", "arrivals": n,
+                       "offered_rate_per_s": 2000.0},
+            "completed": len(lat), "submitted": submitted, "ladmap_iters_per_s": inner / wall,
+            "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
+                           "note": "arrival time to completion (queueing included)"},
+            "gpu_launches": launches, "clocks": clk}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    wl = args.workload if args.workload in ("affine", "small", "projective") else "affine"
     pool, cores = cpu_pool()
     for _ in range(args.warmup):
-        run_oracle_sample(pool, cores, 0.0, max_patches=cores)
+        run_oracle_sample(pool, cores, 0.0, max_patches=cores, workload=wl)
     vals = []
     t_all = 0.0
     n_all = 0
     budget = max(5.0, 120.0 / max(1, args.steps))
     for s in range(args.steps):
-        sample, wall = run_oracle_sample(pool, cores, budget, first=s * 4 * cores)
+        sample, wall = run_oracle_sample(pool, cores, budget, first=s * 4 * cores, workload=wl)
         vals.append(len(sample) / wall)
         t_all += wall
         n_all += len(sample)
@@ -337,7 +457,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "patches_per_gpu": args.patches, "p": 6},
+            "config": {"workload": WORKLOADS[wl][0], "patches_per_gpu": args.patches or WORKLOADS[wl][1], "p": 6},
             "cpu_baseline": {"value": v, "unit": "patches/s", "cores": cores, "kind": "oracle",
                              "cpu": cpu_model(),
                              "sample": f"each step: patches of the same workload for about {budget:.0f} s, "
@@ -362,6 +482,8 @@ def main():
         dist = D
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "stream":
+        out = run_stream(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank, dist)
     if rank == 0 and out is not None:

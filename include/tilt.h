@@ -57,7 +57,8 @@ typedef struct {
     size_t hbm_budget_bytes;    /* device workspace pool; 0 -> 25 % of free memory at create  */
     int max_live;               /* problems admitted at once; 0 -> 65536                      */
     void* cuda_stream;          /* reserved; the context always creates its own streams       */
-    const char* autotune_cache; /* reserved                                                   */
+    const char* autotune_cache; /* file of autotuned group widths (read at create, written by
+                                   tilt_autotune); NULL: tuning lives in the context only     */
 } tilt_config;
 
 /* Solver parameters (Algorithm 1 inputs).  tilt_default_params() fills the defaults;
@@ -135,6 +136,22 @@ typedef struct {
  * problem is admitted or none is (TILT_E_NOMEM / TILT_E_BUSY). */
 int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, int is_device_ptr,
                       const tilt_params* params, uint64_t* tickets_out);
+
+/* Autotuner: for the size bucket ((R+15)/16, (C+15)/16), R = max(m, n), C = min(m, n), of
+ * each of the count shapes (m, n pairs in shapes[2*count]) not tuned yet, time the Jacobi
+ * group widths 4, 8 and 16 (lanes per column pair) on a synthetic grouped launch (one
+ * problem per SM, one outer step of six inner iterations) and keep the fastest for this
+ * context; chosen_out[count] (may be NULL) receives the width of each shape.  The choice
+ * depends only on the bucket, never on the batch a problem is submitted with.  When
+ * tilt_config.autotune_cache names a file, it is read at tilt_create and rewritten here.
+ * Runs synchronously (about 0.1-2 s per new bucket).  Errors: TILT_E_INVAL, TILT_E_CUDA. */
+int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform type, int* chosen_out);
+
+/* Multi-start selection: the same window solved from several initial transforms, results
+ * stored group by group (results[g * starts + s]).  best_out[g] receives the s with the
+ * lowest objective ||A||_* + lambda ||E||_1 among the results with status >= 0, or -1 when
+ * none succeeded.  Ties keep the lower s.  Errors: TILT_E_INVAL. */
+int tilt_best_of(const tilt_result* results, int n_groups, int starts, int* best_out);
 
 /* Non-blocking completion check.  TILT_PENDING while running; TILT_OK once finished, in
  * which case *out (if non-NULL) receives the result, A_out / E_out (host, m x n row-major,

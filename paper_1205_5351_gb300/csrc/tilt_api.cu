@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <fstream>
 #include <map>
 #include <string>
 #include <thread>
@@ -93,7 +94,7 @@ private:
 
 struct Layout {   // byte offsets inside one problem's workspace
     size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, order, total;
-    int smem_svd, minb;
+    int smem_svd, minb, gw;
     size_t smem;
 };
 
@@ -116,6 +117,9 @@ struct Ticket {
     double t_submit = 0, t_done = 0;
     int batch = -1;              // owning grouped launch (order-array lifetime)
     Request req;
+    bool reaped = false;         // finished; result and planes moved to host, device memory released
+    Result res{};
+    std::vector<float> A_host, E_host;   // row-major m x n, filled when reaped
 };
 
 struct Batch {
@@ -157,6 +161,21 @@ struct tilt_ctx {
     StepOut* step_out_dev = nullptr;
     cudaEvent_t ev[6] = {};         // start/end events of the last grouped launches (3 classes)
     int ev_used = 0;
+    // persistent workers serving single submissions
+    int num_sms = 0;
+    int* q_ring = nullptr;          // host-mapped ring of slot indices
+    int* q_ring_dev = nullptr;
+    int* q_ctl = nullptr;           // host-mapped: [0] tail, [1] stop
+    int* q_ctl_dev = nullptr;
+    int* q_head_dev = nullptr;      // device memory
+    int published = 0;
+    cudaStream_t worker_stream = nullptr;
+    cudaEvent_t worker_done = nullptr;
+    bool workers_launched = false;
+    // autotuned Jacobi group width per size bucket ((R+15)/16, (C+15)/16)
+    std::map<std::pair<int, int>, int> tune;
+    int force_gw = 0;               // non-zero while the autotuner times a candidate
+    std::string tune_path;
 };
 
 namespace {
@@ -184,6 +203,14 @@ bool params_ok(const Params& q) {
            q.outer_tol >= 0 && std::isfinite(q.lam) && std::isfinite(q.mu0);
 }
 
+std::pair<int, int> size_bucket(int R, int C) { return {(R + 15) / 16, (C + 15) / 16}; }
+
+int group_width_for(const tilt_ctx* ctx, int R, int C) {
+    if (ctx->force_gw) return ctx->force_gw;
+    auto it = ctx->tune.find(size_bucket(R, C));
+    return it != ctx->tune.end() ? it->second : default_group_width(R, C);
+}
+
 Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_img) {
     Layout L{};
     const Dims d = make_dims(m, n, p);
@@ -198,21 +225,22 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.p = take(S);
     L.mp = take(S);
     L.zg = take((size_t)d.C * d.C * sizeof(float));
-    const size_t svd = svd_smem_bytes(d);
+    // SVD buffers in shared memory as far as they fit, B first (every dot product reads it),
+    // then V, then T (bit 0 B, bit 1 V, bit 2 T); the others in the workspace
     const size_t head = smem_head_bytes();
-    L.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
-    if (L.smem_svd) {
-        L.bg = L.vg = L.tg = 0;
-        L.smem = svd + head;
-        L.minb = (L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;   // the 2-CTA kernel holds R <= 96 in registers
-    } else {
-        const size_t nb = (size_t)d.ldb * d.Cp * sizeof(float), nv = (size_t)d.ldv * d.Cp * sizeof(float);
-        L.bg = take(nb);
-        L.vg = take(nv);
-        L.tg = take(nb);
-        L.smem = head;
-        L.minb = 1;
-    }
+    const size_t nb = (size_t)d.ldb * d.Cp * sizeof(float), nv = (size_t)d.ldv * d.Cp * sizeof(float);
+    int place = 0;
+    if (2 * nb + nv + head <= ctx->max_smem) place = 7;
+    else if (nb + nv + head <= ctx->max_smem) place = 3;
+    else if (nb + head <= ctx->max_smem) place = 1;
+    L.smem_svd = place;
+    L.smem = head + ((place & 1) ? nb : 0) + ((place & 2) ? nv : 0) + ((place & 4) ? nb : 0);
+    L.bg = (place & 1) ? 0 : take(nb);
+    L.vg = (place & 2) ? 0 : take(nv);
+    L.tg = (place & 4) ? 0 : take(nb);
+    L.gw = group_width_for(ctx, d.R, d.C);
+    // the 2-CTA kernel keeps R <= 96 columns in registers
+    L.minb = (place == 7 && L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;
     L.img = copy_img ? take((size_t)H * W * sizeof(float)) : 0;
     L.order = take(sizeof(int));
     L.total = o;
@@ -264,12 +292,11 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.pl.P = reinterpret_cast<float*>(base + L.p);
     pr.pl.Mp = reinterpret_cast<float*>(base + L.mp);
     pr.pl.Zg = reinterpret_cast<float*>(base + L.zg);
-    if (!L.smem_svd) {
-        pr.pl.Bg = reinterpret_cast<float*>(base + L.bg);
-        pr.pl.Vg = reinterpret_cast<float*>(base + L.vg);
-        pr.pl.Tg = reinterpret_cast<float*>(base + L.tg);
-    }
+    pr.pl.Bg = (L.smem_svd & 1) ? nullptr : reinterpret_cast<float*>(base + L.bg);
+    pr.pl.Vg = (L.smem_svd & 2) ? nullptr : reinterpret_cast<float*>(base + L.vg);
+    pr.pl.Tg = (L.smem_svd & 4) ? nullptr : reinterpret_cast<float*>(base + L.tg);
     pr.smem_svd = L.smem_svd;
+    pr.gw = L.gw;
     pr.res = ctx->res_dev + t.slot;
     pr.done = ctx->done_dev + t.slot;
     ctx->done[t.slot] = 0;
@@ -280,7 +307,7 @@ void release_ticket(tilt_ctx* ctx, uint64_t id) {
     auto it = ctx->tickets.find(id);
     if (it == ctx->tickets.end()) return;
     Ticket& t = it->second;
-    if (t.slot >= 0) {
+    if (t.slot >= 0) {                    // (-1: never admitted, -2: already reaped)
         ctx->pool.release(t.ws_off, t.ws_bytes);
         ctx->free_slots.push_back(t.slot);
     }
@@ -294,8 +321,75 @@ void release_ticket(tilt_ctx* ctx, uint64_t id) {
     ctx->tickets.erase(it);
 }
 
+int fetch_plane(tilt_ctx* ctx, const float* dev, int m, int n, float* host);
+
+// Move every finished problem's result and planes to host memory and release its device
+// memory and slot, so that waiting requests can be admitted whatever order the caller
+// polls in.
+int reap_finished(tilt_ctx* ctx) {
+    for (auto& kv : ctx->tickets) {
+        Ticket& t = kv.second;
+        if (t.slot < 0 || t.reaped) continue;
+        if (!reinterpret_cast<volatile int*>(ctx->done)[t.slot]) continue;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        if (t.t_done == 0) t.t_done = now_ms();
+        t.res = ctx->res[t.slot];
+        t.A_host.resize((size_t)t.m * t.n);
+        t.E_host.resize((size_t)t.m * t.n);
+        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.A, t.m, t.n, t.A_host.data());
+        if (rc) return rc;
+        rc = fetch_plane(ctx, ctx->probs[t.slot].pl.E, t.m, t.n, t.E_host.data());
+        if (rc) return rc;
+        ctx->pool.release(t.ws_off, t.ws_bytes);
+        ctx->free_slots.push_back(t.slot);
+        t.slot = -2;     // finished and reaped
+        t.reaped = true;
+    }
+    return TILT_OK;
+}
+
+constexpr int WORKER_IDLE_SPINS = 25000;   // about 50 ms of empty polls before a worker exits
+
+bool workers_running(tilt_ctx* ctx) {
+    return ctx->workers_launched && cudaEventQuery(ctx->worker_done) == cudaErrorNotReady;
+}
+
+// (Re)launch the persistent workers when none is running.
+int ensure_workers(tilt_ctx* ctx) {
+    if (workers_running(ctx)) return TILT_OK;
+    reinterpret_cast<volatile int*>(ctx->q_ctl)[1] = 0;
+    WorkQueue q;
+    q.ring = ctx->q_ring_dev;
+    q.cap = ctx->max_live;
+    q.tail = ctx->q_ctl_dev;
+    q.stop = ctx->q_ctl_dev + 1;
+    q.head = ctx->q_head_dev;
+    q.idle_spins = WORKER_IDLE_SPINS;
+    CUDA_TRY(launch_workers(ctx->probs_dev, q, ctx->num_sms, ctx->max_smem, ctx->worker_stream));
+    CUDA_TRY(cudaEventRecord(ctx->worker_done, ctx->worker_stream));
+    ctx->workers_launched = true;
+    ctx->launches++;
+    return TILT_OK;
+}
+
+// Hand an admitted ticket to the workers: its image is on the device and its descriptor
+// written before the slot is published (release order), then make sure workers run.
+int publish(tilt_ctx* ctx, Ticket& t) {
+    int rc = prepare(ctx, t, ctx->copy_stream);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));
+    ctx->q_ring[ctx->published % ctx->max_live] = t.slot;
+    std::atomic_thread_fence(std::memory_order_release);
+    reinterpret_cast<volatile int*>(ctx->q_ctl)[0] = ++ctx->published;
+    return ensure_workers(ctx);
+}
+
 // Admit as many waiting requests as fit, each as its own launch.
 int admit_waiting(tilt_ctx* ctx) {
+    if (!ctx->waiting.empty()) {
+        int rc = reap_finished(ctx);
+        if (rc) return rc;
+    }
     while (!ctx->waiting.empty() && !ctx->free_slots.empty()) {
         const uint64_t id = ctx->waiting.front();
         auto it = ctx->tickets.find(id);
@@ -307,16 +401,10 @@ int admit_waiting(tilt_ctx* ctx) {
         t.ws_off = off;
         t.slot = ctx->free_slots.back();
         ctx->free_slots.pop_back();
-        cudaStream_t st = ctx->streams[ctx->next_stream++ & 3];
-        int rc = prepare(ctx, t, st);
+        int rc = publish(ctx, t);
         if (rc) return rc;
         t.req.host_copy.clear();
         t.req.host_copy.shrink_to_fit();
-        int* ord = reinterpret_cast<int*>(ctx->pool_base + t.ws_off + t.lay.order);
-        const int slot = t.slot;
-        CUDA_TRY(cudaMemcpyAsync(ord, &slot, sizeof(int), cudaMemcpyHostToDevice, st));
-        CUDA_TRY(launch_solver(ctx->probs_dev, ord, 1, t.lay.minb, t.lay.smem, st));
-        ctx->launches++;
     }
     return TILT_OK;
 }
@@ -433,6 +521,23 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->done_dev, ctx->done, 0));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->step_out_dev, ctx->step_out, 0));
     for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device));
+    CUDA_TRY(cudaHostAlloc(&ctx->q_ring, ns * sizeof(int), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostAlloc(&ctx->q_ctl, 2 * sizeof(int), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->q_ring_dev, ctx->q_ring, 0));
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->q_ctl_dev, ctx->q_ctl, 0));
+    ctx->q_ctl[0] = ctx->q_ctl[1] = 0;
+    if (cfg->autotune_cache) {
+        ctx->tune_path = cfg->autotune_cache;
+        std::ifstream f(ctx->tune_path);
+        int rb, cb, gw;
+        while (f >> rb >> cb >> gw)
+            if (gw == 4 || gw == 8 || gw == 16) ctx->tune[{rb, cb}] = gw;
+    }
+    CUDA_TRY(cudaMalloc(&ctx->q_head_dev, sizeof(int)));
+    CUDA_TRY(cudaMemset(ctx->q_head_dev, 0, sizeof(int)));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->worker_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->worker_done, cudaEventDisableTiming));
     memset(ctx->done, 0, ns * sizeof(int));
     ctx->free_slots.reserve(ns);
     for (int s = (int)ns - 1; s >= 0; --s) ctx->free_slots.push_back(s);
@@ -484,15 +589,9 @@ int tilt_submit(tilt_ctx* ctx, const float* img, int H, int W, size_t ld_elems, 
     t.ws_off = off;
     t.slot = ctx->free_slots.back();
     ctx->free_slots.pop_back();
-    cudaStream_t st = ctx->streams[ctx->next_stream++ & 3];
     auto& tk = ctx->tickets.emplace(id, std::move(t)).first->second;
-    rc = prepare(ctx, tk, st);
+    rc = publish(ctx, tk);
     if (rc) { release_ticket(ctx, id); return rc; }
-    int* ord = reinterpret_cast<int*>(ctx->pool_base + tk.ws_off + tk.lay.order);
-    const int slot = tk.slot;
-    CUDA_TRY(cudaMemcpyAsync(ord, &slot, sizeof(int), cudaMemcpyHostToDevice, st));
-    CUDA_TRY(launch_solver(ctx->probs_dev, ord, 1, tk.lay.minb, tk.lay.smem, st));
-    ctx->launches++;
     *ticket_out = id;
     return TILT_OK;
 }
@@ -625,6 +724,13 @@ int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, fl
     auto it = ctx->tickets.find(ticket);
     if (it == ctx->tickets.end()) return fail(TILT_E_NOTFOUND, "ticket %llu", (unsigned long long)ticket);
     Ticket& t = it->second;
+    if (t.reaped) {
+        if (A_out) memcpy(A_out, t.A_host.data(), sizeof(float) * t.A_host.size());
+        if (E_out) memcpy(E_out, t.E_host.data(), sizeof(float) * t.E_host.size());
+        if (out) fill_result(t.res, t, out);
+        release_ticket(ctx, ticket);
+        return admit_waiting(ctx);
+    }
     if (t.slot < 0) {
         int rc = admit_waiting(ctx);
         if (rc) return rc;
@@ -633,6 +739,13 @@ int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, fl
     if (!reinterpret_cast<volatile int*>(ctx->done)[t.slot]) {
         cudaError_t e = cudaPeekAtLastError();
         if (e != cudaSuccess) return fail(TILT_E_CUDA, "CUDA error while waiting: %s", cudaGetErrorString(e));
+        // a worker only exits when the queue looked empty; if all have exited while this
+        // queued problem is unfinished, it was published after their last look
+        if (t.batch < 0 && ctx->workers_launched && !workers_running(ctx) &&
+            !reinterpret_cast<volatile int*>(ctx->done)[t.slot]) {
+            int rc = ensure_workers(ctx);
+            if (rc) return rc;
+        }
         return TILT_PENDING;
     }
     std::atomic_thread_fence(std::memory_order_acquire);
@@ -651,6 +764,103 @@ int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, fl
     return admit_waiting(ctx);
 }
 
+int tilt_best_of(const tilt_result* results, int n_groups, int starts, int* best_out) {
+    if (!results || !best_out || n_groups < 0 || starts < 1) return fail(TILT_E_INVAL, "bad arguments");
+    for (int g = 0; g < n_groups; ++g) {
+        int best = -1;
+        double bo = 0.0;
+        for (int s = 0; s < starts; ++s) {
+            const tilt_result& r = results[(size_t)g * starts + s];
+            if (r.status < 0 || !std::isfinite(r.objective)) continue;
+            if (best < 0 || r.objective < bo) {
+                best = s;
+                bo = r.objective;
+            }
+        }
+        best_out[g] = best;
+    }
+    return TILT_OK;
+}
+
+int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform type, int* chosen_out) {
+    if (!ctx || (count && !shapes) || count < 0) return fail(TILT_E_INVAL, "bad arguments");
+    if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "bad type");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    bool changed = false;
+    for (int s = 0; s < count; ++s) {
+        const int m = shapes[2 * s], n = shapes[2 * s + 1];
+        if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "shape %d x %d", m, n);
+        const Dims d = make_dims(m, n, (int)type);
+        const auto key = size_bucket(d.R, d.C);
+        if (!ctx->tune.count(key)) {
+            // a smooth synthetic texture with noise, rotated slightly: one outer step of six
+            // inner iterations on one problem per SM for every candidate width
+            const int H = m + 16, W = n + 16;
+            std::vector<float> img((size_t)H * W);
+            uint32_t st = 12345u;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    st = st * 1664525u + 1013904223u;
+                    img[(size_t)y * W + x] = 0.5f + 0.3f * std::sin(0.37f * x) * std::cos(0.23f * y) +
+                                             0.05f * ((st >> 8) * (1.0f / 16777216.0f) - 0.5f);
+                }
+            float* dimg = nullptr;
+            CUDA_TRY(cudaMalloc(&dimg, img.size() * sizeof(float)));
+            CUDA_TRY(cudaMemcpy(dimg, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
+            const int K = ctx->num_sms;
+            std::vector<tilt_problem> probs((size_t)K);
+            for (auto& pb : probs) {
+                memset(&pb, 0, sizeof pb);
+                pb.img = dimg;
+                pb.H = H;
+                pb.W = W;
+                pb.ld_elems = W;
+                pb.m = m;
+                pb.n = n;
+                pb.type = (int)type;
+                const double th = 0.05;
+                pb.tau0[0] = std::cos(th); pb.tau0[1] = -std::sin(th); pb.tau0[2] = 0.5 * (W - 1);
+                pb.tau0[3] = std::sin(th); pb.tau0[4] = std::cos(th); pb.tau0[5] = 0.5 * (H - 1);
+            }
+            tilt_params prm;
+            tilt_default_params(&prm);
+            prm.max_outer = 1;
+            prm.max_inner = 6;
+            prm.eps1 = 0.0;
+            int best = default_group_width(d.R, d.C);
+            float best_ms = 1e30f;
+            const int cands[3] = {4, 8, 16};
+            for (int gw : cands) {
+                if ((d.C + 1) / 2 > 8 * (NT / gw)) continue;    // more than 8 pairs per group per round
+                ctx->force_gw = gw;
+                std::vector<uint64_t> tk((size_t)K);
+                int rc = tilt_submit_batch(ctx, K, probs.data(), 1, &prm, tk.data());
+                ctx->force_gw = 0;
+                if (rc) { cudaFree(dimg); return rc; }
+                float ms[3];
+                const int nl = tilt_batch_kernel_ms(ctx, ms, 3);
+                for (uint64_t t : tk) {
+                    rc = tilt_wait(ctx, t, 600000, nullptr, nullptr, nullptr);
+                    if (rc) { cudaFree(dimg); return rc; }
+                }
+                if (nl <= 0) { cudaFree(dimg); return nl < 0 ? nl : fail(TILT_E_CUDA, "no timing"); }
+                float tot = 0.f;
+                for (int q = 0; q < nl; ++q) tot = std::max(tot, ms[q]);
+                if (tot < best_ms) { best_ms = tot; best = gw; }
+            }
+            CUDA_TRY(cudaFree(dimg));
+            ctx->tune[key] = best;
+            changed = true;
+        }
+        if (chosen_out) chosen_out[s] = ctx->tune[key];
+    }
+    if (changed && !ctx->tune_path.empty()) {
+        std::ofstream f(ctx->tune_path, std::ios::trunc);
+        for (const auto& kv : ctx->tune) f << kv.first.first << ' ' << kv.first.second << ' ' << kv.second << '\n';
+    }
+    return TILT_OK;
+}
+
 int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, float* A_out, float* E_out) {
     const double t_end = now_ms() + (timeout_ms < 0 ? 60000.0 : (double)timeout_ms);
     for (;;) {
@@ -664,11 +874,13 @@ int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, 
 int tilt_destroy(tilt_ctx* ctx) {
     if (!ctx) return TILT_OK;
     cudaSetDevice(ctx->device);
+    reinterpret_cast<volatile int*>(ctx->q_ctl)[1] = 1;     // workers exit once the queue is empty
     const double t_end = now_ms() + 120000.0;
     for (;;) {
         bool busy = false;
         for (auto s : ctx->streams) busy = busy || cudaStreamQuery(s) == cudaErrorNotReady;
         busy = busy || cudaStreamQuery(ctx->copy_stream) == cudaErrorNotReady;
+        busy = busy || cudaStreamQuery(ctx->worker_stream) == cudaErrorNotReady;
         if (!busy) break;
         if (now_ms() > t_end) return fail(TILT_E_TIMEOUT, "work still running after 120 s; context leaked");
         std::this_thread::sleep_for(std::chrono::milliseconds(1));
@@ -676,6 +888,11 @@ int tilt_destroy(tilt_ctx* ctx) {
     for (auto s : ctx->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(ctx->copy_stream);
     for (auto e : ctx->ev) cudaEventDestroy(e);
+    cudaEventDestroy(ctx->worker_done);
+    cudaStreamDestroy(ctx->worker_stream);
+    cudaFree(ctx->q_head_dev);
+    cudaFreeHost(ctx->q_ring);
+    cudaFreeHost(ctx->q_ctl);
     cudaFree(ctx->pool_base);
     if (ctx->scratch) cudaFree(ctx->scratch);
     cudaFreeHost(ctx->probs);

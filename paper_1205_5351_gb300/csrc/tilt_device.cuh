@@ -62,7 +62,8 @@ struct Problem {
     double tau[8];
     Params prm;
     Planes pl;
-    int smem_svd;          // 1: B, V, T live in shared memory
+    int smem_svd;          // bits 0, 1, 2: B, V, T live in shared memory (else Bg, Vg, Tg)
+    int gw;                // Jacobi group width (lanes per column pair): 4, 8 or 16
     Result* res;           // host-mapped result record
     volatile int* done;    // host-mapped completion flag
 };
@@ -543,12 +544,16 @@ __device__ inline RotParams rotation_for(float a, float b, float g, float tol) {
     p.s = 0.f;
     p.r = 0.f;
     if (p.rot) {
+        // square roots as x rsqrt(x): s and r share q, so the applied transform
+        // [[1 - s r, -s], [s, 1 - s r]] stays orthogonal to O(t^2 eps) whatever q's rounding
         p.cosabs = fabsf(g) * rsqrtf(ab);
         const float d = b - a;
         const float w = 2.f * g;
-        const float h = sqrtf(fmaf(d, d, w * w));
+        const float h2 = fmaf(d, d, w * w);
+        const float h = h2 * rsqrtf(h2);
         const float t = __fdividef(w, d + copysignf(h, d));
-        const float q = sqrtf(fmaf(t, t, 1.f));
+        const float q2 = fmaf(t, t, 1.f);
+        const float q = q2 * rsqrtf(q2);
         p.s = __fdividef(t, q);
         p.r = __fdividef(t, 1.f + q);
     }
@@ -582,19 +587,28 @@ __device__ inline void rotate_v(float* V, int ldv, int i, int j, int nqv, int g,
     }
 }
 
+__device__ inline float group_sum(float v, unsigned mask, int gw) {
+    for (int off = 1; off < gw; off <<= 1) v += __shfl_xor_sync(mask, v, off, gw);
+    return v;
+}
+
+// gw (4, 8 or 16) lanes per column pair: NT/gw pairs in flight per CTA, lane g of a group
+// holds the float4 chunks g, g+gw, g+2gw, ... of both columns (in registers while
+// R <= 4 gw NCH).  gw only changes how the work is spread, not the rotation sequence; the
+// partial sums of the dot products are combined in a different order for each gw.
 template <int NCH>
 static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                                int* flag) {
+                                int* flag, int gw) {
     if (C < 2) return 0;
     const int lane = threadIdx.x & 31;
-    const int grp = threadIdx.x >> 3, g = lane & 7;
-    constexpr int NG = NT / 8;
-    const unsigned gmask = 0xFFu << (lane & 24);
+    const int grp = threadIdx.x / gw, g = lane & (gw - 1);
+    const int NG = NT / gw;
+    const unsigned gmask = (gw == 32 ? 0xFFFFFFFFu : ((1u << gw) - 1u)) << (lane & ~(gw - 1));
     const int Ce = C + (C & 1);
     const int npairs = Ce / 2;
     const int nr = Ce - 1;
     const int nqb = ldb / 4, nqv = ldv / 4;
-    const bool in_regs = nqb <= 8 * NCH;     // R <= 32 NCH: NCH chunks per lane hold a column
+    const bool in_regs = nqb <= gw * NCH;
     float* fl = reinterpret_cast<float*>(flag);
     int sweep = 0;
     while (sweep < max_sweeps) {
@@ -618,7 +632,7 @@ static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int
                     float pa[NCH], pb[NCH], pg[NCH];
 #pragma unroll
                     for (int t = 0; t < NCH; ++t) {
-                        const int q = g + 8 * t;
+                        const int q = g + gw * t;
                         if (q < nqb) {
                             x[t] = bi[q];
                             y[t] = bj[q];
@@ -636,41 +650,63 @@ static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int
                         b += pb[t];
                         gg += pg[t];
                     }
-                    a = group8_sum(a, gmask);
-                    b = group8_sum(b, gmask);
-                    gg = group8_sum(gg, gmask);
+                    a = group_sum(a, gmask, gw);
+                    b = group_sum(b, gmask, gw);
+                    gg = group_sum(gg, gmask, gw);
                     const RotParams rp = rotation_for(a, b, gg, tol);
                     if (rp.rot) {
 #pragma unroll
                         for (int t = 0; t < NCH; ++t) {
-                            const int q = g + 8 * t;
+                            const int q = g + gw * t;
                             if (q < nqb) {
                                 bi[q] = rot_x(x[t], y[t], rp.s, rp.r);
                                 bj[q] = rot_y(x[t], y[t], rp.s, rp.r);
                             }
                         }
-                        rotate_v(V, ldv, i, j, nqv, g, rp.s, rp.r);
+                        // V (C <= R rows): the same chunk pattern, unrolled so that all loads
+                        // are in flight together
+                        float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
+                        float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
+#pragma unroll
+                        for (int t = 0; t < NCH; ++t) {
+                            const int q = g + gw * t;
+                            if (q < nqv) { x[t] = vi[q]; y[t] = vj[q]; }
+                        }
+#pragma unroll
+                        for (int t = 0; t < NCH; ++t) {
+                            const int q = g + gw * t;
+                            if (q < nqv) {
+                                vi[q] = rot_x(x[t], y[t], rp.s, rp.r);
+                                vj[q] = rot_y(x[t], y[t], rp.s, rp.r);
+                            }
+                        }
                         rotated = true;
                         maxcos = fmaxf(maxcos, rp.cosabs);
                     }
                 } else {
-                    for (int q = g; q < nqb; q += 8) {
+                    for (int q = g; q < nqb; q += gw) {
                         const float4 x = bi[q], y = bj[q];
                         a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
                         b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
                         gg = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, gg))));
                     }
-                    a = group8_sum(a, gmask);
-                    b = group8_sum(b, gmask);
-                    gg = group8_sum(gg, gmask);
+                    a = group_sum(a, gmask, gw);
+                    b = group_sum(b, gmask, gw);
+                    gg = group_sum(gg, gmask, gw);
                     const RotParams rp = rotation_for(a, b, gg, tol);
                     if (rp.rot) {
-                        for (int q = g; q < nqb; q += 8) {
+                        for (int q = g; q < nqb; q += gw) {
                             const float4 x = bi[q], y = bj[q];
                             bi[q] = rot_x(x, y, rp.s, rp.r);
                             bj[q] = rot_y(x, y, rp.s, rp.r);
                         }
-                        rotate_v(V, ldv, i, j, nqv, g, rp.s, rp.r);
+                        float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
+                        float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
+                        for (int q = g; q < nqv; q += gw) {
+                            const float4 x = vi[q], y = vj[q];
+                            vi[q] = rot_x(x, y, rp.s, rp.r);
+                            vj[q] = rot_y(x, y, rp.s, rp.r);
+                        }
                         rotated = true;
                         maxcos = fmaxf(maxcos, rp.cosabs);
                     }
@@ -690,6 +726,15 @@ static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int
         if (!any || mc * mc < tol) break;
     }
     return sweep;
+}
+
+// Default group width for a C-column matrix: every pair of a round in flight at once when
+// possible, otherwise the widest group that keeps at most two pairs per group.
+__host__ __device__ inline int default_group_width(int R, int C) {
+    const int pairs = (C + 1) / 2;
+    if (pairs <= NT / 16 && R > 64) return 16;
+    if (pairs <= NT / 8) return 8;
+    return 4;
 }
 
 // Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the

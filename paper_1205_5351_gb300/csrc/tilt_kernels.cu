@@ -33,6 +33,60 @@ __global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const 
     }
 }
 
+__device__ inline int load_acquire_sys(const int* p) {
+    int v;
+    asm volatile("ld.acquire.sys.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent worker: thread 0 claims the next published problem (acquire load of the tail,
+// compare-and-swap on the head), the CTA solves it and publishes the result; after
+// idle_spins empty polls (each followed by a ~2 us sleep) or when stop is set, it exits.
+__global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue q) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    __shared__ Problem sp;
+    __shared__ Result sres;
+    __shared__ int claim;
+    SmemLayout L = carve_smem(smem_raw);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int got = -1;
+            for (int idle = 0; idle <= q.idle_spins;) {
+                const int t = load_acquire_sys(q.tail);
+                const int h = atomicAdd(q.head, 0);
+                if (h < t) {
+                    if (atomicCAS(q.head, h, h + 1) == h) {
+                        got = load_acquire_sys(q.ring + (h % q.cap));
+                        break;
+                    }
+                    continue;
+                }
+                if (load_acquire_sys(q.stop)) break;
+                ++idle;
+                __nanosleep(2000);
+            }
+            claim = got;
+        }
+        __syncthreads();
+        const int slot = claim;
+        __syncthreads();
+        if (slot < 0) return;
+        {   // the descriptor was written by the host before the tail was published
+            const volatile int* s = reinterpret_cast<const volatile int*>(probs + slot);
+            int* d = reinterpret_cast<int*>(&sp);
+            for (int w = threadIdx.x; w < (int)(sizeof(Problem) / 4); w += NT) d[w] = s[w];
+            __syncthreads();
+        }
+        solve_problem<4>(sp, L, sres);
+        if (threadIdx.x == 0) {
+            *sp.res = sres;
+            __threadfence_system();
+            *sp.done = 1;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(NT, 1) warp_step_kernel(WarpArgs a) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     SmemLayout L = carve_smem(smem_raw);
@@ -77,7 +131,8 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     }
     __syncthreads();
     set_identity(V, d.ldv, d.Cp);
-    const int sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag);
+    const int sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag,
+                                default_group_width(d.R, d.C));
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
     svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg);
@@ -124,7 +179,8 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     __shared__ Result cyc;
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
-    InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc);
+    InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
+                             default_group_width(d.R, d.C));
     if (threadIdx.x == 0) {
         a.out->status = io.bad ? -1 : 0;
         a.out->iters = io.iters;
@@ -144,6 +200,8 @@ cudaError_t configure_kernels(size_t max_smem) {
         return e;
     if ((e = cudaFuncSetAttribute(svt_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
+    if ((e = cudaFuncSetAttribute(worker_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
     if ((e = cudaFuncSetAttribute(inner_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
     return cudaSuccess;
@@ -155,6 +213,11 @@ cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb,
         solver_kernel<2, 3><<<count, NT, smem, st>>>(probs, order);
     else
         solver_kernel<1, 4><<<count, NT, smem, st>>>(probs, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_workers(Problem* probs, const WorkQueue& q, int ctas, size_t smem, cudaStream_t st) {
+    worker_kernel<<<ctas, NT, smem, st>>>(probs, q);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,21 @@ struct InnerArgs {
     StepOut* out;
 };
 
+// Work queue of the persistent workers.  ring/tail/stop live in host-mapped memory (written
+// by the host), head in device memory (claimed by the workers with atomicCAS).
+struct WorkQueue {
+    const int* ring;        // slot indices, cap entries
+    int cap;
+    const int* tail;        // entries published so far (host writes with release order)
+    const int* stop;        // non-zero: workers exit when idle
+    int* head;              // entries claimed so far
+    int idle_spins;         // bounded idle wait (x ~2 us) before a worker exits
+};
+
+// Persistent workers: `ctas` CTAs claim problems from the queue until it stays empty for
+// idle_spins polls (or stop is set), each solving one problem at a time.
+cudaError_t launch_workers(Problem* probs, const WorkQueue& q, int ctas, size_t smem, cudaStream_t st);
+
 // Solver: count CTAs, CTA b solves probs[order[b]].  minb selects the occupancy variant.
 cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st);
 cudaError_t launch_warp_step(const WarpArgs& a, cudaStream_t st);

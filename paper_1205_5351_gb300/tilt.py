@@ -51,6 +51,14 @@ class Result(ctypes.Structure):
                 ("svd_warm", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("kkt_residual", ctypes.c_double),
                 ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5)]
 
+    @classmethod
+    def from_dict(cls, d: dict) -> "Result":
+        r = cls()
+        r.status, r.p, r.objective = d["status"], d["p"], d["objective"]
+        for k, v in enumerate(d["tau"]):
+            r.tau[k] = float(v)
+        return r
+
     def to_dict(self) -> dict:
         return dict(status=self.status, p=self.p, tau=np.array(self.tau[: self.p]), objective=self.objective,
                     lam=self.lambda_, rank=self.rank_A, outer_iters=self.outer_iters,
@@ -88,6 +96,8 @@ SIGNATURES = {
     "tilt_inner": (_i, [_vp, _vp, _vp, _i, _i, _P(_d), _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d),
                         _P(_d), _P(_d), _P(_d)]),
     "tilt_svt_noalloc": (_i, [_vp, _i, _i, ctypes.c_float, _vp, _vp, _vp]),
+    "tilt_best_of": (_i, [_P(Result), _i, _i, _P(_i)]),
+    "tilt_autotune": (_i, [_vp, _P(_i), _i, _i, _P(_i)]),
 }
 
 _lib = None
@@ -127,6 +137,16 @@ def _dptr(t) -> int:
     return t.data_ptr()
 
 
+def best_of(results: list, starts: int) -> list:
+    """Multi-start selection (tilt_best_of): per group of `starts` consecutive results, the
+    index of the lowest objective among successful ones (-1 if none)."""
+    n = len(results) // starts
+    arr = (Result * (n * starts))(*[Result.from_dict(r) for r in results[: n * starts]])
+    out = (ctypes.c_int * max(1, n))()
+    _check(lib().tilt_best_of(arr, n, starts, out))
+    return [out[i] for i in range(n)]
+
+
 # ------------------------------------------------------------------ layout marshalling
 def dims(m: int, n: int):
     return (m, n) if m >= n else (n, m)
@@ -158,8 +178,9 @@ def jacobian_from_rows(J: np.ndarray, m: int, n: int) -> np.ndarray:
 class Context:
     """One solver context on one device (``tilt_create`` / ``tilt_destroy``)."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_live: int = 0):
-        cfg = Config(device, hbm_budget_bytes, max_live, None, None)
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_live: int = 0, autotune_cache: str = None):
+        self._cache = autotune_cache.encode() if autotune_cache else None
+        cfg = Config(device, hbm_budget_bytes, max_live, None, self._cache)
         h = _vp()
         _check(lib().tilt_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h
@@ -185,6 +206,14 @@ class Context:
     @property
     def launches(self) -> int:
         return int(lib().tilt_kernel_launches(self.h))
+
+    def autotune(self, shapes, ttype: int = AFFINE) -> list:
+        """Tune the Jacobi group width for the size buckets of the given (m, n) shapes."""
+        shapes = list(shapes)
+        arr = (ctypes.c_int * (2 * max(1, len(shapes))))(*[v for mn in shapes for v in mn])
+        out = (ctypes.c_int * max(1, len(shapes)))()
+        _check(lib().tilt_autotune(self.h, arr, len(shapes), ttype, out), self.h)
+        return [out[i] for i in range(len(shapes))]
 
     def batch_kernel_ms(self) -> list:
         """Device time (ms) of each grouped launch of the last submit_batch (CUDA events)."""

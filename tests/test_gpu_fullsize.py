@@ -1,0 +1,62 @@
+"""Full-size workloads in the benchmark's launch configuration (one grouped submission, device
+images), checked against the oracle on sampled patches and, for every patch, on properties
+that hold at any size."""
+import numpy as np
+import pytest
+
+from oracle import tilt_oracle as O
+from paper_1205_5351_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1205_5351_gb300 import build, tilt
+    build.build()
+    return tilt
+
+
+def _run(T, patches, prm=None):
+    with T.Context(0) as ctx:
+        items = [(torch.from_numpy(p.img).cuda(), p.m, p.n, p.tau0, p.ttype) for p in patches]
+        tickets = ctx.submit_batch(items, prm, on_device=True)
+        return [ctx.wait(t, 1800000) for t in tickets]
+
+
+def _properties(T, patches, res, eps1):
+    for p, r in zip(patches, res):
+        assert r["status"] in (0, 1, 2), r["status"]
+        assert np.all(np.isfinite(r["tau"])) and np.isfinite(r["objective"]) and r["objective"] > 0
+        assert 1 <= r["rank"] <= min(p.m, p.n)
+        assert 1 <= r["outer_iters"] <= 10
+        # an inner loop that stopped did so on Cond1 (status 2: it hit max_inner instead)
+        assert r["status"] == 2 or r["kkt"] < eps1
+        # the constraint Q dtau = 0 keeps the window centre (affine: exactly the translation)
+        if p.ttype == 6:
+            assert abs(r["tau"][2] - p.tau0[2]) < 1e-6 and abs(r["tau"][5] - p.tau0[5]) < 1e-6
+
+
+def test_affine_batch_1024_full_size(T):
+    patches = synth.mixed_affine_batch(1024)
+    res = _run(T, patches)
+    _properties(T, patches, res, 1e-5)
+    for q in (0, 201, 402, 603, 804, 1005):
+        p = patches[q]
+        ref = O.tilt(p.img.astype(np.float64), p.tau0, p.ttype, p.m, p.n, O.Params())
+        assert O.tau_error(res[q]["tau"], ref.tau) <= 1e-3, q
+        assert res[q]["rank"] == ref.rank, q
+
+
+def test_projective_batch_256_full_size(T):
+    patches = synth.projective_batch(256)
+    res = _run(T, patches)
+    _properties(T, patches, res, 1e-5)
+    p = patches[17]
+    ref = O.tilt(p.img.astype(np.float64), p.tau0, p.ttype, p.m, p.n, O.Params())
+    assert O.tau_error(res[17]["tau"], ref.tau) <= 1e-3
+    assert res[17]["rank"] == ref.rank
