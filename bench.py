@@ -71,6 +71,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stream-seconds", type=float, default=600.0, help="wall-clock cap of the served stream")
+    ap.add_argument("--no-autotune", action="store_true", help="skip autotuning (profiling captures)")
     ap.add_argument("--max-outer", type=int, default=None, help="override (small profiling cases only)")
     ap.add_argument("--max-inner", type=int, default=None, help="override (small profiling cases only)")
     return ap.parse_args()
@@ -237,7 +238,9 @@ def run_ours(args, rank, world, local_rank, dist):
 
     # autotune the Jacobi group width for every size bucket of the workload (untimed)
     t_tune = time.perf_counter()
-    ctx.autotune(sorted({(p.m, p.n) for p in patches}), patches[0].ttype)
+    widths = []
+    if not args.no_autotune:
+        widths = ctx.autotune(sorted({(p.m, p.n) for p in patches}), patches[0].ttype)
     tune_s = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         step(items_dev, True, False)
@@ -325,6 +328,8 @@ def run_ours(args, rank, world, local_rank, dist):
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA issue rate)"},
             "gpu_launches": launches // max(1, args.steps),
             "autotune_s": round(tune_s, 2),
+            "autotune_schedules": {("gw%d%s" % (w & 255, "-block" if w >> 8 else "")): widths.count(w)
+                                   for w in sorted(set(widths))},
             "clocks": clk,
             "e2e": {"value": n_total / (float(tot[1]) * 1e-3), "unit": "patches/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

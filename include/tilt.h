@@ -57,7 +57,7 @@ typedef struct {
     size_t hbm_budget_bytes;    /* device workspace pool; 0 -> 25 % of free memory at create  */
     int max_live;               /* problems admitted at once; 0 -> 65536                      */
     void* cuda_stream;          /* reserved; the context always creates its own streams       */
-    const char* autotune_cache; /* file of autotuned group widths (read at create, written by
+    const char* autotune_cache; /* file of autotuned Jacobi schedules (read at create, written by
                                    tilt_autotune); NULL: tuning lives in the context only     */
 } tilt_config;
 
@@ -139,9 +139,11 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, in
 
 /* Autotuner: for the size bucket ((R+15)/16, (C+15)/16), R = max(m, n), C = min(m, n), of
  * each of the count shapes (m, n pairs in shapes[2*count]) not tuned yet, time the Jacobi
- * group widths 4, 8 and 16 (lanes per column pair) on a synthetic grouped launch (one
- * problem per SM, one outer step of six inner iterations) and keep the fastest for this
- * context; chosen_out[count] (may be NULL) receives the width of each shape.  The choice
+ * schedules (group width 4, 8 or 16 lanes per column pair, times round-robin or
+ * block-cyclic pair ordering) on a synthetic grouped launch (one problem per SM, one outer
+ * step of 30 inner iterations) and keep the fastest for this context; chosen_out[count]
+ * (may be NULL) receives the schedule of each shape: the width, plus 256 for block-cyclic
+ * ordering.  Both orderings visit every column pair once per sweep.  The choice
  * depends only on the bucket, never on the batch a problem is submitted with.  When
  * tilt_config.autotune_cache names a file, it is read at tilt_create and rewritten here.
  * Runs synchronously (about 0.1-2 s per new bucket).  Errors: TILT_E_INVAL, TILT_E_CUDA. */

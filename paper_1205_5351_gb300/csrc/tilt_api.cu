@@ -94,7 +94,7 @@ private:
 
 struct Layout {   // byte offsets inside one problem's workspace
     size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, order, total;
-    int smem_svd, minb, gw;
+    int smem_svd, minb, jsched;
     size_t smem;
 };
 
@@ -174,7 +174,7 @@ struct tilt_ctx {
     bool workers_launched = false;
     // autotuned Jacobi group width per size bucket ((R+15)/16, (C+15)/16)
     std::map<std::pair<int, int>, int> tune;
-    int force_gw = 0;               // non-zero while the autotuner times a candidate
+    int force_js = 0;               // non-zero while the autotuner times a candidate schedule
     std::string tune_path;
 };
 
@@ -205,10 +205,17 @@ bool params_ok(const Params& q) {
 
 std::pair<int, int> size_bucket(int R, int C) { return {(R + 15) / 16, (C + 15) / 16}; }
 
-int group_width_for(const tilt_ctx* ctx, int R, int C) {
-    if (ctx->force_gw) return ctx->force_gw;
+// Jacobi schedule for an R x C problem: the autotuned one for its size bucket, else the
+// default group width with round-robin ordering.
+int jsched_for(const tilt_ctx* ctx, int R, int C) {
+    if (ctx->force_js) return ctx->force_js;
     auto it = ctx->tune.find(size_bucket(R, C));
     return it != ctx->tune.end() ? it->second : default_group_width(R, C);
+}
+
+bool jsched_valid(int js) {
+    const int w = jsched_width(js), o = jsched_order(js);
+    return (w == 4 || w == 8 || w == 16) && (o == 0 || o == 1);
 }
 
 Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_img) {
@@ -238,7 +245,7 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.bg = (place & 1) ? 0 : take(nb);
     L.vg = (place & 2) ? 0 : take(nv);
     L.tg = (place & 4) ? 0 : take(nb);
-    L.gw = group_width_for(ctx, d.R, d.C);
+    L.jsched = jsched_for(ctx, d.R, d.C);
     // the 2-CTA kernel keeps R <= 96 columns in registers
     L.minb = (place == 7 && L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;
     L.img = copy_img ? take((size_t)H * W * sizeof(float)) : 0;
@@ -296,7 +303,7 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.pl.Vg = (L.smem_svd & 2) ? nullptr : reinterpret_cast<float*>(base + L.vg);
     pr.pl.Tg = (L.smem_svd & 4) ? nullptr : reinterpret_cast<float*>(base + L.tg);
     pr.smem_svd = L.smem_svd;
-    pr.gw = L.gw;
+    pr.jsched = L.jsched;
     pr.res = ctx->res_dev + t.slot;
     pr.done = ctx->done_dev + t.slot;
     ctx->done[t.slot] = 0;
@@ -530,9 +537,9 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     if (cfg->autotune_cache) {
         ctx->tune_path = cfg->autotune_cache;
         std::ifstream f(ctx->tune_path);
-        int rb, cb, gw;
-        while (f >> rb >> cb >> gw)
-            if (gw == 4 || gw == 8 || gw == 16) ctx->tune[{rb, cb}] = gw;
+        int rb, cb, js;
+        while (f >> rb >> cb >> js)
+            if (jsched_valid(js)) ctx->tune[{rb, cb}] = js;
     }
     CUDA_TRY(cudaMalloc(&ctx->q_head_dev, sizeof(int)));
     CUDA_TRY(cudaMemset(ctx->q_head_dev, 0, sizeof(int)));
@@ -793,8 +800,8 @@ int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform ty
         const Dims d = make_dims(m, n, (int)type);
         const auto key = size_bucket(d.R, d.C);
         if (!ctx->tune.count(key)) {
-            // a smooth synthetic texture with noise, rotated slightly: one outer step of six
-            // inner iterations on one problem per SM for every candidate width
+            // a smooth synthetic texture with noise, rotated slightly: one outer step of 30
+            // inner iterations on one problem per SM for every candidate schedule
             const int H = m + 16, W = n + 16;
             std::vector<float> img((size_t)H * W);
             uint32_t st = 12345u;
@@ -825,17 +832,18 @@ int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform ty
             tilt_params prm;
             tilt_default_params(&prm);
             prm.max_outer = 1;
-            prm.max_inner = 6;
+            prm.max_inner = 30;      // long enough that warm-started SVDs dominate, as in real solves
             prm.eps1 = 0.0;
             int best = default_group_width(d.R, d.C);
             float best_ms = 1e30f;
-            const int cands[3] = {4, 8, 16};
-            for (int gw : cands) {
+            const int widths[3] = {4, 8, 16};
+            for (int c = 0; c < 6; ++c) {
+                const int gw = widths[c % 3], js = gw | (c >= 3 ? JSCHED_BLOCK : 0);
                 if ((d.C + 1) / 2 > 8 * (NT / gw)) continue;    // more than 8 pairs per group per round
-                ctx->force_gw = gw;
+                ctx->force_js = js;
                 std::vector<uint64_t> tk((size_t)K);
                 int rc = tilt_submit_batch(ctx, K, probs.data(), 1, &prm, tk.data());
-                ctx->force_gw = 0;
+                ctx->force_js = 0;
                 if (rc) { cudaFree(dimg); return rc; }
                 float ms[3];
                 const int nl = tilt_batch_kernel_ms(ctx, ms, 3);
@@ -846,7 +854,7 @@ int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform ty
                 if (nl <= 0) { cudaFree(dimg); return nl < 0 ? nl : fail(TILT_E_CUDA, "no timing"); }
                 float tot = 0.f;
                 for (int q = 0; q < nl; ++q) tot = std::max(tot, ms[q]);
-                if (tot < best_ms) { best_ms = tot; best = gw; }
+                if (tot < best_ms) { best_ms = tot; best = js; }
             }
             CUDA_TRY(cudaFree(dimg));
             ctx->tune[key] = best;

@@ -63,7 +63,8 @@ struct Problem {
     Params prm;
     Planes pl;
     int smem_svd;          // bits 0, 1, 2: B, V, T live in shared memory (else Bg, Vg, Tg)
-    int gw;                // Jacobi group width (lanes per column pair): 4, 8 or 16
+    int jsched;            // Jacobi schedule: bits 0-7 group width (lanes per column pair: 4, 8
+                           // or 16), bit 8 block-cyclic pair ordering (else round-robin)
     Result* res;           // host-mapped result record
     volatile int* done;    // host-mapped completion flag
 };
@@ -588,6 +589,7 @@ __device__ inline void rotate_v(float* V, int ldv, int i, int j, int nqv, int g,
 }
 
 __device__ inline float group_sum(float v, unsigned mask, int gw) {
+#pragma unroll
     for (int off = 1; off < gw; off <<= 1) v += __shfl_xor_sync(mask, v, off, gw);
     return v;
 }
@@ -596,136 +598,227 @@ __device__ inline float group_sum(float v, unsigned mask, int gw) {
 // holds the float4 chunks g, g+gw, g+2gw, ... of both columns (in registers while
 // R <= 4 gw NCH).  gw only changes how the work is spread, not the rotation sequence; the
 // partial sums of the dot products are combined in a different order for each gw.
-template <int NCH>
-static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                                int* flag, int gw) {
-    if (C < 2) return 0;
-    const int lane = threadIdx.x & 31;
-    const int grp = threadIdx.x / gw, g = lane & (gw - 1);
-    const int NG = NT / gw;
+
+// One pair step of the one-sided Jacobi for columns i, j, executed by a group of gw lanes
+// (lane g of the group holds float4 chunks g, g+gw, ... ; in registers while nqb <= gw NCH).
+template <int NCH, int gw>
+__device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, int j, int nqb, int nqv, int g,
+                                   unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
+    float4* bi = reinterpret_cast<float4*>(B + (size_t)i * ldb);
+    float4* bj = reinterpret_cast<float4*>(B + (size_t)j * ldb);
+    float a = 0.f, b = 0.f, gg = 0.f;
+    if (in_regs) {
+        float4 x[NCH], y[NCH];
+        float pa[NCH], pb[NCH], pg[NCH];
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            const int q = g + gw * t;
+            if (q < nqb) {
+                x[t] = bi[q];
+                y[t] = bj[q];
+            } else {
+                x[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                y[t] = x[t];
+            }
+            pa[t] = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, x[t].w * x[t].w)));
+            pb[t] = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, y[t].w * y[t].w)));
+            pg[t] = fmaf(x[t].x, y[t].x, fmaf(x[t].y, y[t].y, fmaf(x[t].z, y[t].z, x[t].w * y[t].w)));
+        }
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+            a += pa[t];
+            b += pb[t];
+            gg += pg[t];
+        }
+        a = group_sum(a, gmask, gw);
+        b = group_sum(b, gmask, gw);
+        gg = group_sum(gg, gmask, gw);
+        const RotParams rp = rotation_for(a, b, gg, tol);
+        if (rp.rot) {
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int q = g + gw * t;
+                if (q < nqb) {
+                    bi[q] = rot_x(x[t], y[t], rp.s, rp.r);
+                    bj[q] = rot_y(x[t], y[t], rp.s, rp.r);
+                }
+            }
+            // V (C <= R rows): the same chunk pattern, unrolled so that all loads are in flight
+            float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
+            float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int q = g + gw * t;
+                if (q < nqv) { x[t] = vi[q]; y[t] = vj[q]; }
+            }
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+                const int q = g + gw * t;
+                if (q < nqv) {
+                    vi[q] = rot_x(x[t], y[t], rp.s, rp.r);
+                    vj[q] = rot_y(x[t], y[t], rp.s, rp.r);
+                }
+            }
+            rotated = true;
+            maxcos = fmaxf(maxcos, rp.cosabs);
+        }
+    } else {
+        for (int q = g; q < nqb; q += gw) {
+            const float4 x = bi[q], y = bj[q];
+            a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
+            b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
+            gg = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, gg))));
+        }
+        a = group_sum(a, gmask, gw);
+        b = group_sum(b, gmask, gw);
+        gg = group_sum(gg, gmask, gw);
+        const RotParams rp = rotation_for(a, b, gg, tol);
+        if (rp.rot) {
+            for (int q = g; q < nqb; q += gw) {
+                const float4 x = bi[q], y = bj[q];
+                bi[q] = rot_x(x, y, rp.s, rp.r);
+                bj[q] = rot_y(x, y, rp.s, rp.r);
+            }
+            float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
+            float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
+            for (int q = g; q < nqv; q += gw) {
+                const float4 x = vi[q], y = vj[q];
+                vi[q] = rot_x(x, y, rp.s, rp.r);
+                vj[q] = rot_y(x, y, rp.s, rp.r);
+            }
+            rotated = true;
+            maxcos = fmaxf(maxcos, rp.cosabs);
+        }
+    }
+}
+
+// End of a sweep: did any pair rotate, and the largest rotated cosine (all threads).
+__device__ inline bool sweep_done(bool rotated, float maxcos, float tol, int* flag) {
+    float* fl = reinterpret_cast<float*>(flag);
+    if (rotated) {
+        flag[0] = 1;
+        atomicMax(reinterpret_cast<int*>(&fl[1]), __float_as_int(maxcos));   // non-negative floats order as ints
+    }
+    __syncthreads();
+    const int any = flag[0];
+    const float mc = fl[1];
+    __syncthreads();
+    return !any || mc * mc < tol;
+}
+
+// Column-pair ordering of the sweeps.  0: round-robin over columns (C-1 rounds of disjoint
+// pairs, a CTA barrier after each).  1: block-cyclic: the columns form 2 W blocks of b
+// columns (W warps); in each of the 2W-1 block rounds a warp owns a block pair and works
+// through its b^2 cross pairs (b sub-rounds of b disjoint pairs, __syncwarp between them;
+// in the first block round of a sweep also the pairs inside each of its blocks), a CTA
+// barrier after each block round.  Both visit every pair once per sweep.
+// The group width is a template parameter: the shuffle widths and chunk indices sit on the
+// critical path of every pair step.
+template <int NCH, int gw>
+static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
+                                  int* flag, int order) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane & (gw - 1);
     const unsigned gmask = (gw == 32 ? 0xFFFFFFFFu : ((1u << gw) - 1u)) << (lane & ~(gw - 1));
-    const int Ce = C + (C & 1);
-    const int npairs = Ce / 2;
-    const int nr = Ce - 1;
     const int nqb = ldb / 4, nqv = ldv / 4;
     const bool in_regs = nqb <= gw * NCH;
-    float* fl = reinterpret_cast<float*>(flag);
     int sweep = 0;
+    if (order == 0) {
+        const int grp = threadIdx.x / gw;
+        const int NG = NT / gw;
+        const int Ce = C + (C & 1);
+        const int npairs = Ce / 2;
+        const int nr = Ce - 1;
+        while (sweep < max_sweeps) {
+            if (threadIdx.x == 0) { flag[0] = 0; reinterpret_cast<float*>(flag)[1] = 0.f; }
+            __syncthreads();
+            bool rotated = false;
+            float maxcos = 0.f;
+            for (int round = 0; round < nr; ++round) {
+                for (int k = grp; k < npairs; k += NG) {
+                    int i = 0;
+                    if (k) { i = k - 1 + round; if (i >= nr) i -= nr; i += 1; }
+                    int j = Ce - 2 - k + round;
+                    if (j >= nr) j -= nr;
+                    j += 1;
+                    if (i >= C || j >= C) continue;
+                    jacobi_pair<NCH, gw>(B, ldb, V, ldv, i, j, nqb, nqv, g, gmask, tol, in_regs, rotated, maxcos);
+                }
+                __syncthreads();
+            }
+            ++sweep;
+            if (sweep_done(rotated, maxcos, tol, flag)) break;
+        }
+        return sweep;
+    }
+    // block-cyclic
+    const int gpw = 32 / gw;                       // groups per warp
+    const int gi = lane / gw;                      // group index within the warp
+    int b = (C + 2 * NW - 1) / (2 * NW);           // block width
+    if (b < gpw) b = gpw;
+    b += b & 1;                                    // even, for the round-robin inside a block
+    int NB = (C + b - 1) / b;
+    NB += NB & 1;
+    const int nbr = NB - 1;                        // block rounds per sweep
+    const int nwu = NB / 2;                        // warps with a block pair
     while (sweep < max_sweeps) {
-        if (threadIdx.x == 0) { flag[0] = 0; fl[1] = 0.f; }
+        if (threadIdx.x == 0) { flag[0] = 0; reinterpret_cast<float*>(flag)[1] = 0.f; }
         __syncthreads();
         bool rotated = false;
         float maxcos = 0.f;
-        for (int round = 0; round < nr; ++round) {
-            for (int k = grp; k < npairs; k += NG) {
-                int i = 0;
-                if (k) { i = k - 1 + round; if (i >= nr) i -= nr; i += 1; }
-                int j = Ce - 2 - k + round;
-                if (j >= nr) j -= nr;
-                j += 1;
-                if (i >= C || j >= C) continue;
-                float4* bi = reinterpret_cast<float4*>(B + (size_t)i * ldb);
-                float4* bj = reinterpret_cast<float4*>(B + (size_t)j * ldb);
-                float a = 0.f, b = 0.f, gg = 0.f;
-                if (in_regs) {
-                    float4 x[NCH], y[NCH];
-                    float pa[NCH], pb[NCH], pg[NCH];
-#pragma unroll
-                    for (int t = 0; t < NCH; ++t) {
-                        const int q = g + gw * t;
-                        if (q < nqb) {
-                            x[t] = bi[q];
-                            y[t] = bj[q];
-                        } else {
-                            x[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            y[t] = x[t];
+        for (int br = 0; br < nbr; ++br) {
+            if (warp < nwu) {
+                int P = 0;
+                if (warp) { P = warp - 1 + br; if (P >= nbr) P -= nbr; P += 1; }
+                int Q = NB - 2 - warp + br;
+                if (Q >= nbr) Q -= nbr;
+                Q += 1;
+                if (br == 0) {
+                    // pairs inside blocks P and Q: round-robin over b columns, b-1 sub-rounds of b/2
+                    for (int sr = 0; sr < b - 1; ++sr) {
+                        for (int k = gi; k < b; k += gpw) {
+                            const int blk = (k < b / 2) ? P : Q;
+                            const int kk = (k < b / 2) ? k : k - b / 2;
+                            int li = 0;
+                            if (kk) { li = kk - 1 + sr; if (li >= b - 1) li -= b - 1; li += 1; }
+                            int lj = b - 2 - kk + sr;
+                            if (lj >= b - 1) lj -= b - 1;
+                            lj += 1;
+                            const int ci = blk * b + li, cj = blk * b + lj;
+                            if (ci < C && cj < C)
+                                jacobi_pair<NCH, gw>(B, ldb, V, ldv, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
+                                                     rotated, maxcos);
                         }
-                        pa[t] = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, x[t].w * x[t].w)));
-                        pb[t] = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, y[t].w * y[t].w)));
-                        pg[t] = fmaf(x[t].x, y[t].x, fmaf(x[t].y, y[t].y, fmaf(x[t].z, y[t].z, x[t].w * y[t].w)));
+                        __syncwarp();
                     }
-#pragma unroll
-                    for (int t = 0; t < NCH; ++t) {
-                        a += pa[t];
-                        b += pb[t];
-                        gg += pg[t];
+                }
+                for (int s = 0; s < b; ++s) {
+                    for (int a = gi; a < b; a += gpw) {
+                        int c = a + s;
+                        if (c >= b) c -= b;
+                        const int ci = P * b + a, cj = Q * b + c;
+                        if (ci < C && cj < C)
+                            jacobi_pair<NCH, gw>(B, ldb, V, ldv, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
+                                                 rotated, maxcos);
                     }
-                    a = group_sum(a, gmask, gw);
-                    b = group_sum(b, gmask, gw);
-                    gg = group_sum(gg, gmask, gw);
-                    const RotParams rp = rotation_for(a, b, gg, tol);
-                    if (rp.rot) {
-#pragma unroll
-                        for (int t = 0; t < NCH; ++t) {
-                            const int q = g + gw * t;
-                            if (q < nqb) {
-                                bi[q] = rot_x(x[t], y[t], rp.s, rp.r);
-                                bj[q] = rot_y(x[t], y[t], rp.s, rp.r);
-                            }
-                        }
-                        // V (C <= R rows): the same chunk pattern, unrolled so that all loads
-                        // are in flight together
-                        float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
-                        float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
-#pragma unroll
-                        for (int t = 0; t < NCH; ++t) {
-                            const int q = g + gw * t;
-                            if (q < nqv) { x[t] = vi[q]; y[t] = vj[q]; }
-                        }
-#pragma unroll
-                        for (int t = 0; t < NCH; ++t) {
-                            const int q = g + gw * t;
-                            if (q < nqv) {
-                                vi[q] = rot_x(x[t], y[t], rp.s, rp.r);
-                                vj[q] = rot_y(x[t], y[t], rp.s, rp.r);
-                            }
-                        }
-                        rotated = true;
-                        maxcos = fmaxf(maxcos, rp.cosabs);
-                    }
-                } else {
-                    for (int q = g; q < nqb; q += gw) {
-                        const float4 x = bi[q], y = bj[q];
-                        a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
-                        b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
-                        gg = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, gg))));
-                    }
-                    a = group_sum(a, gmask, gw);
-                    b = group_sum(b, gmask, gw);
-                    gg = group_sum(gg, gmask, gw);
-                    const RotParams rp = rotation_for(a, b, gg, tol);
-                    if (rp.rot) {
-                        for (int q = g; q < nqb; q += gw) {
-                            const float4 x = bi[q], y = bj[q];
-                            bi[q] = rot_x(x, y, rp.s, rp.r);
-                            bj[q] = rot_y(x, y, rp.s, rp.r);
-                        }
-                        float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
-                        float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
-                        for (int q = g; q < nqv; q += gw) {
-                            const float4 x = vi[q], y = vj[q];
-                            vi[q] = rot_x(x, y, rp.s, rp.r);
-                            vj[q] = rot_y(x, y, rp.s, rp.r);
-                        }
-                        rotated = true;
-                        maxcos = fmaxf(maxcos, rp.cosabs);
-                    }
+                    __syncwarp();
                 }
             }
             __syncthreads();
         }
-        if (rotated) {
-            flag[0] = 1;
-            atomicMax(reinterpret_cast<int*>(&fl[1]), __float_as_int(maxcos));   // non-negative floats order as ints
-        }
-        __syncthreads();
-        const int any = flag[0];
-        const float mc = fl[1];
-        __syncthreads();
         ++sweep;
-        if (!any || mc * mc < tol) break;
+        if (sweep_done(rotated, maxcos, tol, flag)) break;
     }
     return sweep;
+}
+
+template <int NCH>
+static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
+                                int* flag, int gw, int order) {
+    if (C < 2) return 0;
+    if (gw == 4) return k2_jacobi_w<NCH, 4>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
+    if (gw == 16) return k2_jacobi_w<NCH, 16>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
+    return k2_jacobi_w<NCH, 8>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
 }
 
 // Default group width for a C-column matrix: every pair of a round in flight at once when
@@ -736,6 +829,10 @@ __host__ __device__ inline int default_group_width(int R, int C) {
     if (pairs <= NT / 8) return 8;
     return 4;
 }
+
+constexpr int JSCHED_BLOCK = 256;   // schedule bit: block-cyclic pair ordering
+__host__ __device__ inline int jsched_width(int js) { return js & 255; }
+__host__ __device__ inline int jsched_order(int js) { return js >> 8; }
 
 // Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the
 // list of kept columns.  Returns (via scal) sum (sigma - eps)_+, max (sigma - eps)_+ and

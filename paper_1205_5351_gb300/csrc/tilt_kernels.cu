@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     __syncthreads();
     set_identity(V, d.ldv, d.Cp);
     const int sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag,
-                                default_group_width(d.R, d.C));
+                                default_group_width(d.R, d.C), 0);
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
     svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg);

@@ -44,7 +44,7 @@ template <int NCH>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
-                            bool& haveV, const SmemLayout& L, Result* cyc, int gw) {
+                            bool& haveV, const SmemLayout& L, Result* cyc, int jsched) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
     InnerOut out;
@@ -139,7 +139,8 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
             set_identity(buf.V, ldv, Cp);
         }
-        const int sw = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag, gw);
+        const int sw = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
+                                      jsched_width(jsched), jsched_order(jsched));
         haveV = true;
         out.sweeps += sw;
         const float eps = (float)(1.0 / mu);
@@ -380,7 +381,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
             if (threadIdx.x == 0) res.cyc_other += clk() - t1;
             InnerOut io = k_inner<NCH>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
-                                  pr.pl.Mp, buf, haveV, L, &res, pr.gw);
+                                  pr.pl.Mp, buf, haveV, L, &res, pr.jsched);
             inner_total += io.iters;
             sweeps += io.sweeps;
             warm += io.warm;

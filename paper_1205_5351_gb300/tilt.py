@@ -208,7 +208,8 @@ class Context:
         return int(lib().tilt_kernel_launches(self.h))
 
     def autotune(self, shapes, ttype: int = AFFINE) -> list:
-        """Tune the Jacobi group width for the size buckets of the given (m, n) shapes."""
+        """Tune the Jacobi schedule for the size buckets of the given (m, n) shapes; returns each
+        shape's schedule (group width, plus 256 for block-cyclic pair ordering)."""
         shapes = list(shapes)
         arr = (ctypes.c_int * (2 * max(1, len(shapes))))(*[v for mn in shapes for v in mn])
         out = (ctypes.c_int * max(1, len(shapes)))()
