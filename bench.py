@@ -26,7 +26,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+METRIC = "patches rectified/s & LADMAP iters/s at \u03c4 err\u22641e-3 vs plain GPU; p50/p99 latency"
 WORKLOAD = ("1024 affine (p=6) patches, sides uniform 40-120 (non-square), rank 1-5 textures or "
             "checkerboards of period 4-16, rotation +-30 deg, skew +-0.2, corruption 0-10 %")
 
@@ -57,6 +57,26 @@ def make_patches(workload, count, first):
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grouped launch of the solver
+# kernel, by workload and launch class, from one ncu capture of the full-size workload (the
+# command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
+# sources they were taken on: when the SHA-256 of csrc/ and include/ differs, traffic is null.
+NCU_TRAFFIC = {"sources_sha256": "9e2c6a960b185d1095093c5cb7e192b68c42c65aee5e7914a98b74ab04c7947a",
+               "bytes": {"affine/1024/0": 13637756160 + 17846582272,
+                         "affine/1024/1": 10106382592 + 14146849280}}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    dirs = [os.path.join(ROOT, "paper_1205_5351_gb300", "csrc"), os.path.join(ROOT, "include")]
+    for d in dirs:
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".cuh", ".h")):
+                h.update(f.encode())
+                h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()
 
 
 def parse_args():
@@ -283,11 +303,21 @@ def run_ours(args, rank, world, local_rank, dist):
     if rank == 0:
         flops = [algorithmic_flops(p, r) for p, r in zip(patches, results)]
         k_ms = statistics.mean(sum(k) for k in kernel_ms) if kernel_ms and kernel_ms[0] else None
-        # the classes run concurrently; the dominant launch is the longest one
-        k_dom = statistics.mean(max(k) for k in kernel_ms) if kernel_ms and kernel_ms[0] else None
-        achieved = sum(flops) / (k_dom * 1e-3) / 1e12 if k_dom else None
+        # one grouped launch per class present (ascending class order), run concurrently on
+        # their own streams; the dominant launch is the one with the longest mean duration
+        classes = sorted({r["launch_class"] for r in results})
+        per_class_ms = [statistics.mean(k[i] for k in kernel_ms) for i in range(len(classes))] \
+            if kernel_ms and kernel_ms[0] and len(kernel_ms[0]) == len(classes) else []
+        dom = max(range(len(per_class_ms)), key=lambda i: per_class_ms[i]) if per_class_ms else None
+        k_dom = per_class_ms[dom] if dom is not None else None
+        dom_class = classes[dom] if dom is not None else None
+        dom_flops = sum(f for f, r in zip(flops, results) if r["launch_class"] == dom_class)
+        achieved = dom_flops / (k_dom * 1e-3) / 1e12 if k_dom else None
         mhz = MAX_SM_MHZ
         peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        traffic = None
+        if NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha256() and not over and not args.no_autotune:
+            traffic = NCU_TRAFFIC["bytes"].get("%s/%s/%s" % (args.workload, len(patches), dom_class))
         out = {
             "metric": METRIC,
             "value": None,
@@ -315,7 +345,10 @@ def run_ours(args, rank, world, local_rank, dist):
                                     [round(sum(r["phase_cycles"][i] for r in results) /
                                            max(1, sum(sum(r["phase_cycles"]) for r in results)), 4)
                                      for i in range(5)])),
-            "kernel_ms": {"sum_of_launches": k_ms, "longest_launch": k_dom},
+            "kernel_ms": {"sum_of_launches": k_ms, "longest_launch": k_dom,
+                          "per_class": {str(c): t for c, t in zip(classes, per_class_ms)},
+                          "patches_per_class": {str(c): sum(1 for r in results if r["launch_class"] == c)
+                                                for c in classes}},
             "slowest_patch": (lambda q: {"m": patches[q].m, "n": patches[q].n, "kind": patches[q].meta["kind"],
                                          "done_ms": lat[q], "outer": results[q]["outer_iters"],
                                          "inner": results[q]["inner_iters"], "sweeps": results[q]["svd_sweeps"],
@@ -323,8 +356,11 @@ def run_ours(args, rank, world, local_rank, dist):
                                          "phase_mcycles": [round(c / 1e6, 2) for c in results[q]["phase_cycles"]]})(
                 int(np.argmax(lat[-len(results):]))),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel": "solver_kernel (fused Algorithm 1, one CTA per patch)",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "kernel": "solver_kernel launch of class %s (fused Algorithm 1, one CTA per patch, "
+                                   "%d patches)" % (dom_class, sum(1 for r in results
+                                                               if r["launch_class"] == dom_class)),
+                         "flops_per_launch": dom_flops,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA issue rate)"},
             "gpu_launches": launches // max(1, args.steps),
             "autotune_s": round(tune_s, 2),

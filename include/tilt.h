@@ -98,6 +98,10 @@ typedef struct {
     uint64_t phase_cycles[5]; /* SM clock cycles of the solve by phase: warp + Jacobian, SVD
                                  (Jacobi sweeps + warm-start product), SVT reconstruction,
                                  elementwise passes (E, Y, M), other (Gram, ||D||_2)          */
+    int launch_class;    /* grouped launch that solved it (tilt_submit_batch): 0 two CTAs per
+                            SM, all SVD buffers in shared memory; 1 one CTA per SM, the SVD
+                            buffers in shared memory as far as they fit; 2 one CTA per SM, all
+                            in device memory.  -1: solved by the persistent worker CTAs      */
 } tilt_result;
 
 /* Fill *p with the default parameters. */

@@ -416,6 +416,10 @@ int admit_waiting(tilt_ctx* ctx) {
     return TILT_OK;
 }
 
+// Grouped-launch class of a problem: 0 two CTAs per SM (all SVD buffers in shared memory),
+// 1 one CTA per SM (shared memory as far as it holds them), 2 one CTA per SM (none).
+int launch_class_of(const Layout& L) { return L.smem_svd ? (L.minb == 2 ? 0 : 1) : 2; }
+
 void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     memset(out, 0, sizeof *out);
     out->status = r.status;
@@ -436,6 +440,7 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->phase_cycles[2] = r.cyc_recon;
     out->phase_cycles[3] = r.cyc_elem;
     out->phase_cycles[4] = r.cyc_other;
+    out->launch_class = t.batch < 0 ? -1 : launch_class_of(t.lay);
 }
 
 // Copy a device plane (long-side-contiguous) to a host m x n row-major array.
@@ -639,7 +644,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
     std::vector<int> idx(count);
     for (int q = 0; q < count; ++q) idx[q] = q;
     std::vector<int> klass(count);
-    for (int q = 0; q < count; ++q) klass[q] = ts[q].lay.smem_svd ? (ts[q].lay.minb == 2 ? 0 : 1) : 2;
+    for (int q = 0; q < count; ++q) klass[q] = launch_class_of(ts[q].lay);
     auto cls = [&](int q) { return klass[q]; };
     auto cost = [&](int q) {
         const Dims d = make_dims(ts[q].m, ts[q].n, ts[q].p);

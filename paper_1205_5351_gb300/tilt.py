@@ -49,7 +49,8 @@ class Result(ctypes.Structure):
                 ("objective", ctypes.c_double), ("lambda_", ctypes.c_double), ("rank_A", ctypes.c_int),
                 ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("svd_sweeps", ctypes.c_int),
                 ("svd_warm", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("kkt_residual", ctypes.c_double),
-                ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5)]
+                ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5),
+                ("launch_class", ctypes.c_int)]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Result":
@@ -64,7 +65,7 @@ class Result(ctypes.Structure):
                     lam=self.lambda_, rank=self.rank_A, outer_iters=self.outer_iters,
                     inner_iters=self.inner_iters, svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm,
                     oob=self.oob_pixels, kkt=self.kkt_residual, latency_ms=self.latency_ms,
-                    phase_cycles=list(self.phase_cycles))
+                    phase_cycles=list(self.phase_cycles), launch_class=self.launch_class)
 
 
 class Problem(ctypes.Structure):
