@@ -70,8 +70,12 @@ typedef struct {
     double rho0;       /* Eq. rho growth factor, >= 1 (default 1.5)                           */
     double mu0;        /* initial penalty of every inner loop; <= 0 -> 1.25 / ||D_hat||_2     */
     double mu_max;     /* Eq. mu upper bound (default 1e10)                                   */
-    double eps_svd;    /* SVD warm-start gate (Alg. 2): warm when ||M_k - M_k-1||_F <
-                          eps_svd * ||M_k||_F (default 0.05); < 0 -> always warm             */
+    double eps_svd;    /* SVD warm-start gate (the gate of Alg. 2): warm-start the Jacobi SVD
+                          from the previous V when ||M_k - M_k-1||_F < eps_svd ||M_k||_F;
+                          < 0 (default): whenever the previous V is valid.  The warm-started
+                          Jacobi converges to the exact SVD for any change of M (it never
+                          took more sweeps than a cold start in measurements), unlike the
+                          approximate Cayley step that Alg. 2 gates                          */
     int max_inner;     /* inner iterations per outer step (default 500)                       */
     int max_outer;     /* outer steps (default 10)                                            */
     double outer_tol;  /* stop when dtau moves no window corner by more than this many

@@ -491,7 +491,7 @@ void tilt_default_params(tilt_params* p) {
     p->rho0 = 1.5;
     p->mu0 = -1.0;
     p->mu_max = 1e10;
-    p->eps_svd = 0.05;
+    p->eps_svd = -1.0;      // the Jacobi warm start is exact: use it whenever V is valid
     p->max_inner = 500;
     p->max_outer = 10;
     p->outer_tol = 1e-2;

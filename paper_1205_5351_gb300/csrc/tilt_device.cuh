@@ -695,9 +695,13 @@ __device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, 
 // End of a sweep: did any pair rotate, and the largest rotated cosine (all threads).
 __device__ inline bool sweep_done(bool rotated, float maxcos, float tol, int* flag) {
     float* fl = reinterpret_cast<float*>(flag);
-    if (rotated) {
+    const bool any_w = __any_sync(0xFFFFFFFFu, rotated);
+    float mc_w = maxcos;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mc_w = fmaxf(mc_w, __shfl_xor_sync(0xFFFFFFFFu, mc_w, o));
+    if (any_w && (threadIdx.x & 31) == 0) {
         flag[0] = 1;
-        atomicMax(reinterpret_cast<int*>(&fl[1]), __float_as_int(maxcos));   // non-negative floats order as ints
+        atomicMax(reinterpret_cast<int*>(&fl[1]), __float_as_int(mc_w));   // non-negative floats order as ints
     }
     __syncthreads();
     const int any = flag[0];
