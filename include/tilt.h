@@ -86,7 +86,8 @@ typedef struct {
 typedef struct {
     int status;          /* 0 outer loop converged, 1 max_outer reached, 2 some inner loop hit
                             max_inner (tau still valid), < 0 numeric failure (-1 non-finite,
-                            -2 singular J^T J + Q^T Q, -3 zero image window)                  */
+                            -2 singular J^T J + Q^T Q, -3 zero image window), -4 cancelled
+                            by tilt_destroy (tau = the last completed outer step's)           */
     int p;               /* 6 or 8                                                             */
     double tau[8];       /* final transform (first p entries)                                 */
     double objective;    /* ||A||_* + lambda ||E||_1 of the last inner loop (Eq. TILT_2)       */
@@ -175,9 +176,11 @@ int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, fl
 int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, float* A_out,
               float* E_out);
 
-/* Wait (bounded, 120 s) for all work, free everything.  Returns TILT_E_TIMEOUT if work was
- * still running when the wait expired (resources are then leaked, never freed under a
- * running kernel). */
+/* Cancel and free: running solves stop after their current inner iteration, queued and
+ * not yet started problems are retired unsolved (status -4), the persistent workers exit;
+ * then wait (bounded, 120 s) for the device to finish and free everything.  Returns
+ * TILT_E_TIMEOUT if work was still running when the wait expired (resources are then
+ * leaked, never freed under a running kernel). */
 int tilt_destroy(tilt_ctx* ctx);
 
 /* Message of the last error on the calling thread ("" if none).  ctx is unused. */

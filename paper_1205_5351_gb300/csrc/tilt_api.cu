@@ -165,7 +165,7 @@ struct tilt_ctx {
     int num_sms = 0;
     int* q_ring = nullptr;          // host-mapped ring of slot indices
     int* q_ring_dev = nullptr;
-    int* q_ctl = nullptr;           // host-mapped: [0] tail, [1] stop
+    int* q_ctl = nullptr;           // host-mapped: [0] tail, [1] stop, [2] cancel
     int* q_ctl_dev = nullptr;
     int* q_head_dev = nullptr;      // device memory
     int published = 0;
@@ -306,6 +306,7 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.jsched = L.jsched;
     pr.res = ctx->res_dev + t.slot;
     pr.done = ctx->done_dev + t.slot;
+    pr.cancel = ctx->q_ctl_dev + 2;
     ctx->done[t.slot] = 0;
     return TILT_OK;
 }
@@ -370,6 +371,7 @@ int ensure_workers(tilt_ctx* ctx) {
     q.cap = ctx->max_live;
     q.tail = ctx->q_ctl_dev;
     q.stop = ctx->q_ctl_dev + 1;
+    q.cancel = ctx->q_ctl_dev + 2;
     q.head = ctx->q_head_dev;
     q.idle_spins = WORKER_IDLE_SPINS;
     CUDA_TRY(launch_workers(ctx->probs_dev, q, ctx->num_sms, ctx->max_smem, ctx->worker_stream));
@@ -535,10 +537,10 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device));
     CUDA_TRY(cudaHostAlloc(&ctx->q_ring, ns * sizeof(int), cudaHostAllocMapped));
-    CUDA_TRY(cudaHostAlloc(&ctx->q_ctl, 2 * sizeof(int), cudaHostAllocMapped));
+    CUDA_TRY(cudaHostAlloc(&ctx->q_ctl, 4 * sizeof(int), cudaHostAllocMapped));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->q_ring_dev, ctx->q_ring, 0));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->q_ctl_dev, ctx->q_ctl, 0));
-    ctx->q_ctl[0] = ctx->q_ctl[1] = 0;
+    ctx->q_ctl[0] = ctx->q_ctl[1] = ctx->q_ctl[2] = ctx->q_ctl[3] = 0;
     if (cfg->autotune_cache) {
         ctx->tune_path = cfg->autotune_cache;
         std::ifstream f(ctx->tune_path);
@@ -887,7 +889,11 @@ int tilt_wait(tilt_ctx* ctx, uint64_t ticket, int timeout_ms, tilt_result* out, 
 int tilt_destroy(tilt_ctx* ctx) {
     if (!ctx) return TILT_OK;
     cudaSetDevice(ctx->device);
-    reinterpret_cast<volatile int*>(ctx->q_ctl)[1] = 1;     // workers exit once the queue is empty
+    // running solves stop after their current inner iteration (status -4), queued ones are
+    // retired unsolved, and the workers exit
+    reinterpret_cast<volatile int*>(ctx->q_ctl)[2] = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    reinterpret_cast<volatile int*>(ctx->q_ctl)[1] = 1;
     const double t_end = now_ms() + 120000.0;
     for (;;) {
         bool busy = false;

@@ -67,7 +67,16 @@ struct Problem {
                            // or 16), bit 8 block-cyclic pair ordering (else round-robin)
     Result* res;           // host-mapped result record
     volatile int* done;    // host-mapped completion flag
+    const int* cancel;     // host-mapped: non-zero when the context is being destroyed
 };
+
+// Non-zero once the host has asked running problems to stop (read by thread 0).
+__device__ inline int cancel_requested(const int* cancel) {
+    if (!cancel) return 0;
+    int v;
+    asm volatile("ld.relaxed.sys.u32 %0, [%1];" : "=r"(v) : "l"(cancel) : "memory");
+    return v;
+}
 
 struct Dims {
     int m, n, R, C, S, p;

@@ -42,6 +42,8 @@ __device__ inline int load_acquire_sys(const int* p) {
 // Persistent worker: thread 0 claims the next published problem (acquire load of the tail,
 // compare-and-swap on the head), the CTA solves it and publishes the result; after
 // idle_spins empty polls (each followed by a ~2 us sleep) or when stop is set, it exits.
+// Once cancel is set, claimed problems are retired unsolved (status -4) and a running
+// solve stops after its current inner iteration.
 __global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue q) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     __shared__ Problem sp;
@@ -77,7 +79,17 @@ __global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue
             for (int w = threadIdx.x; w < (int)(sizeof(Problem) / 4); w += NT) d[w] = s[w];
             __syncthreads();
         }
-        solve_problem<4>(sp, L, sres);
+        if (cancel_requested(q.cancel)) {
+            if (threadIdx.x == 0) {
+                memset(&sres, 0, sizeof sres);
+                sres.status = -4;
+                sres.p = sp.p;
+                for (int k = 0; k < PMAX; ++k) sres.tau[k] = sp.tau[k];
+            }
+            __syncthreads();
+        } else {
+            solve_problem<4>(sp, L, sres);
+        }
         if (threadIdx.x == 0) {
             *sp.res = sres;
             __threadfence_system();
@@ -180,7 +192,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
     InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
-                             default_group_width(d.R, d.C));
+                             default_group_width(d.R, d.C), nullptr);
     if (threadIdx.x == 0) {
         a.out->status = io.bad ? -1 : 0;
         a.out->iters = io.iters;

@@ -77,6 +77,7 @@ struct WorkQueue {
     int cap;
     const int* tail;        // entries published so far (host writes with release order)
     const int* stop;        // non-zero: workers exit when idle
+    const int* cancel;      // non-zero: claimed problems are retired unsolved
     int* head;              // entries claimed so far
     int idle_spins;         // bounded idle wait (x ~2 us) before a worker exits
 };

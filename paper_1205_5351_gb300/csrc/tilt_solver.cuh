@@ -8,7 +8,7 @@ namespace tilt {
 
 struct InnerOut {
     int iters, sweeps, warm, rank;
-    bool converged, bad;
+    bool converged, bad, cancelled;
     double c1, c2, mu_last, nuc, l1;
 };
 
@@ -44,11 +44,12 @@ template <int NCH>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
-                            bool& haveV, const SmemLayout& L, Result* cyc, int jsched) {
+                            bool& haveV, const SmemLayout& L, Result* cyc, int jsched, const int* cancel) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
     InnerOut out;
     out.iters = 0; out.sweeps = 0; out.warm = 0; out.rank = 0;
+    out.cancelled = false;
     out.converged = false; out.bad = false;
     out.c1 = out.c2 = 0.0; out.mu_last = mu0; out.nuc = 0.0; out.l1 = 0.0;
     unsigned long long t0 = clk();
@@ -286,6 +287,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                 sc->scal[10] = dacc[0];
                 sc->scal[5] = dacc[1];
                 sc->scal[6] = dacc[2];
+                sc->iscal[7] = cancel_requested(cancel);
             }
             __syncthreads();
         }
@@ -296,6 +298,10 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         out.mu_last = mu;
         if (!isfinite(c1) || !isfinite(c2)) {
             out.bad = true;
+            break;
+        }
+        if (sc->iscal[7]) {          // the context is being destroyed: stop after this iteration
+            out.cancelled = true;
             break;
         }
         if (c1 < prm.eps1 && c2 < prm.eps2) {
@@ -347,18 +353,24 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
     const double lam = prm.lam > 0.0 ? prm.lam : 1.0 / sqrt((double)max(pr.m, pr.n));
     if (threadIdx.x < PMAX) sc->tau[threadIdx.x] = threadIdx.x < pr.p ? pr.tau[threadIdx.x] : 0.0;
     res.cyc_warp = res.cyc_svd = res.cyc_recon = res.cyc_elem = res.cyc_other = 0;
+    if (threadIdx.x == 0) {
+        sc->iscal[7] = cancel_requested(pr.cancel);
+        sc->iscal[0] = 0;
+    }
     __syncthreads();
 
-    int status = 1;
+    int status = sc->iscal[7] ? -4 : 1;
     bool inner_maxed = false;
     int outer = 0, inner_total = 0, sweeps = 0, warm = 0, rank = 0;
     double c1 = 0.0, nuc = 0.0, l1 = 0.0;
     bool haveV = false;
 
     unsigned long long t0 = clk();
-    k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
+    if (status != -4) k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
     if (threadIdx.x == 0) res.cyc_warp += clk() - t0;
-    if (!(sc->scal[0] > 0.0)) {
+    if (status == -4) {
+        // cancelled before it started: tau stays tau0
+    } else if (!(sc->scal[0] > 0.0)) {
         status = -3;
     } else {
         for (int e = threadIdx.x; e < S; e += NT) {     // A_0 = D_hat (R9), E_0 = Y_0 = 0
@@ -381,12 +393,13 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
             if (threadIdx.x == 0) res.cyc_other += clk() - t1;
             InnerOut io = k_inner<NCH>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
-                                  pr.pl.Mp, buf, haveV, L, &res, pr.jsched);
+                                  pr.pl.Mp, buf, haveV, L, &res, pr.jsched, pr.cancel);
             inner_total += io.iters;
             sweeps += io.sweeps;
             warm += io.warm;
             c1 = io.c1; nuc = io.nuc; l1 = io.l1; rank = io.rank;
             if (io.bad) { status = -1; break; }
+            if (io.cancelled) { status = -4; break; }
             if (!io.converged) inner_maxed = true;
             // Steps 3-4: dtau = G^-1 J^T (A + E - D_hat) (= sc->cvec), tau <- tau + dtau
             if (threadIdx.x == 0) {

@@ -1,6 +1,8 @@
 """Serving behaviour through the C ABI: results are the same alone and in a mix, problems
 that do not fit the device-memory budget wait and run when earlier ones retire, and the
 error paths return their codes."""
+import time
+
 import numpy as np
 import pytest
 
@@ -79,3 +81,23 @@ def test_error_codes(T):
         with pytest.raises(T.TiltError) as e:
             ctx.submit(p.img, p.m, p.n, p.tau0, p.ttype, bad)
         assert e.value.code == T.TILT_E_INVAL
+
+
+def test_destroy_cancels_running_and_queued_work(T):
+    # 200 x 200 projective windows take seconds each; destroying the context right after
+    # submitting a grouped launch and more work to the persistent workers must not wait for
+    # them: running solves stop after their current inner iteration, queued ones unsolved
+    patches = synth.projective_batch(24, first=900)
+    ctx = T.Context(0)
+    ctx.submit_batch([(p.img, p.m, p.n, p.tau0, p.ttype) for p in patches[:16]], None)
+    for p in patches[16:]:
+        ctx.submit(p.img, p.m, p.n, p.tau0, p.ttype)
+    time.sleep(0.5)
+    t0 = time.perf_counter()
+    ctx.close()
+    assert time.perf_counter() - t0 < 10.0
+    # a new context on the same device works afterwards
+    q = _stream(40)[0]
+    with T.Context(0) as ctx2:
+        r = ctx2.wait(ctx2.submit(q.img, q.m, q.n, q.tau0, q.ttype, T.default_params(max_outer=1)), 300000)
+    assert r["status"] in (0, 1, 2)
