@@ -155,7 +155,8 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, in
  * ordering.  Both orderings visit every column pair once per sweep.  The choice
  * depends only on the bucket, never on the batch a problem is submitted with.  When
  * tilt_config.autotune_cache names a file, it is read at tilt_create and rewritten here.
- * Runs synchronously (about 0.1-2 s per new bucket).  Errors: TILT_E_INVAL, TILT_E_CUDA. */
+ * Each candidate runs twice and keeps its faster run.  Runs synchronously (about 0.2-4 s
+ * per new bucket).  Errors: TILT_E_INVAL, TILT_E_CUDA. */
 int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform type, int* chosen_out);
 
 /* Multi-start selection: the same window solved from several initial transforms, results
