@@ -248,6 +248,16 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.jsched = jsched_for(ctx, d.R, d.C);
     // the 2-CTA kernel keeps R <= 96 columns in registers
     L.minb = (place == 7 && L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;
+    // the C x C SVT coefficients too, where they fit without changing the occupancy class
+    // (bit 3); else they stay in the workspace
+    {
+        const size_t nz = (size_t)d.C * d.C * sizeof(float);
+        const size_t lim = L.minb == 2 ? (size_t)100 * 1024 : ctx->max_smem;
+        if (place && L.smem + nz <= lim) {
+            L.smem_svd |= 8;
+            L.smem += nz;
+        }
+    }
     L.img = copy_img ? take((size_t)H * W * sizeof(float)) : 0;
     L.order = take(sizeof(int));
     L.total = o;

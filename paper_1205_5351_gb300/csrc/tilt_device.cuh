@@ -62,7 +62,7 @@ struct Problem {
     double tau[8];
     Params prm;
     Planes pl;
-    int smem_svd;          // bits 0, 1, 2: B, V, T live in shared memory (else Bg, Vg, Tg)
+    int smem_svd;          // bits 0-3: B, V, T, Z live in shared memory (else Bg, Vg, Tg, Zg)
     int jsched;            // Jacobi schedule: bits 0-7 group width (lanes per column pair: 4, 8
                            // or 16), bit 8 block-cyclic pair ordering (else round-robin)
     Result* res;           // host-mapped result record
@@ -923,6 +923,44 @@ static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, con
         if (g == 0) {
             const float sg = sigma[k];
             Z[(size_t)q * C + c] = s * (w[k] / (sg * sg));
+        }
+    }
+    __syncthreads();
+}
+
+// The same coefficients as a register-tiled product (inside the solver): each thread owns a
+// 2 x 2 tile of Z (two kept columns of B times two columns of X) and runs over the rows in
+// float4 steps, so every shared-memory load feeds four FMAs.  Consecutive threads take
+// consecutive column pairs of X with the same kept pair (the B loads are broadcasts).
+// Padding rows (R..ldx) of X and B are zero.
+static __device__ void svt_coeffs_tiled(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb,
+                                        int R, int C, const float* sigma, const float* w, const int* kept, int nk,
+                                        float* __restrict__ Z) {
+    const int nq2 = (nk + 1) >> 1, nc2 = (C + 1) >> 1;
+    const int nr4 = (R + 3) >> 2;
+    for (int t = threadIdx.x; t < nq2 * nc2; t += NT) {
+        const int qp = t / nc2, cp = t - qp * nc2;
+        const int q0 = 2 * qp, q1 = min(q0 + 1, nk - 1);
+        const int c0 = 2 * cp, c1 = min(c0 + 1, C - 1);
+        const int k0 = kept[q0], k1 = kept[q1];
+        const float4* b0 = reinterpret_cast<const float4*>(B + (size_t)k0 * ldb);
+        const float4* b1 = reinterpret_cast<const float4*>(B + (size_t)k1 * ldb);
+        const float4* x0 = reinterpret_cast<const float4*>(X + (size_t)c0 * ldx);
+        const float4* x1 = reinterpret_cast<const float4*>(X + (size_t)c1 * ldx);
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+        for (int r = 0; r < nr4; ++r) {
+            const float4 u0 = b0[r], u1 = b1[r], v0 = x0[r], v1 = x1[r];
+            s00 = fmaf(u0.x, v0.x, fmaf(u0.y, v0.y, fmaf(u0.z, v0.z, fmaf(u0.w, v0.w, s00))));
+            s01 = fmaf(u0.x, v1.x, fmaf(u0.y, v1.y, fmaf(u0.z, v1.z, fmaf(u0.w, v1.w, s01))));
+            s10 = fmaf(u1.x, v0.x, fmaf(u1.y, v0.y, fmaf(u1.z, v0.z, fmaf(u1.w, v0.w, s10))));
+            s11 = fmaf(u1.x, v1.x, fmaf(u1.y, v1.y, fmaf(u1.z, v1.z, fmaf(u1.w, v1.w, s11))));
+        }
+        const float f0 = w[k0] / (sigma[k0] * sigma[k0]), f1 = w[k1] / (sigma[k1] * sigma[k1]);
+        Z[(size_t)q0 * C + c0] = s00 * f0;
+        if (c1 != c0) Z[(size_t)q0 * C + c1] = s01 * f0;
+        if (q1 != q0) {
+            Z[(size_t)q1 * C + c0] = s10 * f1;
+            if (c1 != c0) Z[(size_t)q1 * C + c1] = s11 * f1;
         }
     }
     __syncthreads();

@@ -153,36 +153,48 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         const int nk = sc->iscal[1];
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
-        svt_left_coeffs(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z);
+        svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z);
         {
             float acc[1 + PMAX];
 #pragma unroll
             for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
-            // four consecutive rows of one column per thread: float4 reads of B
-            const int nq = (R + 3) >> 2;
-            for (int idx = threadIdx.x; idx < nq * C; idx += NT) {
-                const int c = idx / nq, r0 = (idx - c * nq) * 4;
-                float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            // four consecutive rows of two columns per thread: a float4 of B feeds eight FMAs;
+            // consecutive threads take consecutive row quads (the Z loads are broadcasts)
+            const int nq = (R + 3) >> 2, nc2 = (C + 1) >> 1;
+            for (int idx = threadIdx.x; idx < nq * nc2; idx += NT) {
+                const int cp = idx / nq, r0 = (idx - cp * nq) * 4;
+                const int c0 = 2 * cp, c1 = min(c0 + 1, C - 1);
+                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
                 for (int q = 0; q < nk; ++q) {
                     const float4 b4 = *reinterpret_cast<const float4*>(buf.B + (size_t)L.kept[q] * ldb + r0);
-                    const float z = buf.Z[(size_t)q * C + c];
-                    s4.x = fmaf(b4.x, z, s4.x);
-                    s4.y = fmaf(b4.y, z, s4.y);
-                    s4.z = fmaf(b4.z, z, s4.z);
-                    s4.w = fmaf(b4.w, z, s4.w);
+                    const float z0 = buf.Z[(size_t)q * C + c0], z1 = buf.Z[(size_t)q * C + c1];
+                    s0.x = fmaf(b4.x, z0, s0.x);
+                    s0.y = fmaf(b4.y, z0, s0.y);
+                    s0.z = fmaf(b4.z, z0, s0.z);
+                    s0.w = fmaf(b4.w, z0, s0.w);
+                    s1.x = fmaf(b4.x, z1, s1.x);
+                    s1.y = fmaf(b4.y, z1, s1.y);
+                    s1.z = fmaf(b4.z, z1, s1.z);
+                    s1.w = fmaf(b4.w, z1, s1.w);
                 }
-                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (r0 + u >= R) break;
-                    const int e = c * R + r0 + u;
-                    const float sa = sv[u];
-                    const float da = sa - A[e];
-                    acc[0] = fmaf(da, da, acc[0]);
-                    A[e] = sa;
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && c1 == c0) break;
+                    const int c = h ? c1 : c0;
+                    const float4 s4 = h ? s1 : s0;
+                    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                    for (int k2 = 0; k2 < PMAX; ++k2)
-                        if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+                    for (int u = 0; u < 4; ++u) {
+                        if (r0 + u >= R) break;
+                        const int e = c * R + r0 + u;
+                        const float sa = sv[u];
+                        const float da = sa - A[e];
+                        acc[0] = fmaf(da, da, acc[0]);
+                        A[e] = sa;
+#pragma unroll
+                        for (int k2 = 0; k2 < PMAX; ++k2)
+                            if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+                    }
                 }
             }
             double dacc[1 + PMAX];
@@ -341,9 +353,9 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
         const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
         if (pr.smem_svd & 1) { buf.B = sm; sm += nb; } else { buf.B = pr.pl.Bg; }
         if (pr.smem_svd & 2) { buf.V = sm; sm += nv; } else { buf.V = pr.pl.Vg; }
-        if (pr.smem_svd & 4) { buf.T = sm; } else { buf.T = pr.pl.Tg; }
+        if (pr.smem_svd & 4) { buf.T = sm; sm += nb; } else { buf.T = pr.pl.Tg; }
+        buf.Z = (pr.smem_svd & 8) ? sm : pr.pl.Zg;      // SVT coefficients (C x C)
     }
-    buf.Z = pr.pl.Zg;
     // zero the SVD buffers (padding rows/columns are read by the tiled GEMM)
     {
         const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
