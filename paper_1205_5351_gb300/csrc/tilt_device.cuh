@@ -115,7 +115,8 @@ struct Scratch {
     double cvec[PMAX];         // coefficients c = G^-1 J^T (.) of the current W^T W product
     double tau[PMAX];
     double dtau[PMAX];
-    double scal[16];           // broadcast scalars
+    double scal[20];           // broadcast scalars
+    float fs[16];              // per-iteration float scalars, computed by thread 0 (FS_*)
     int iscal[8];
     int flag[2];
 };
@@ -178,6 +179,32 @@ __device__ inline void block_sum(double (&v)[K], double* red) {
     for (int k = 0; k < K; ++k) v[k] = red[48 * NW - 1 - k];
     __syncthreads();
 }
+
+// Per-iteration variant for FP32 partials: FP32 shuffle tree in every warp, then one thread
+// per value adds the NW warp totals in FP64.  No per-thread FP64 arithmetic (on this part
+// an FP64 operation issued by all 512 threads costs as much as ~32 of FP32).  The totals are
+// left in red[48 NW - 1 - k] (read them after the final barrier).
+template <int K>
+__device__ inline void block_sum_f(float (&v)[K], double* red) {
+    static_assert(K <= 44, "block_sum staging: 48 values per warp, the last 44 slots also hold the totals");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float f = v[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+        if (lane == 0) red[k * NW + warp] = (double)f;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += red[threadIdx.x * NW + w];
+        red[48 * NW - 1 - threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+__device__ inline double block_total(const double* red, int k) { return red[48 * NW - 1 - k]; }
 
 // Exact-order FP64 variant for the once-per-outer-step reductions (norms of the warp, the
 // Gram matrix, the warm-start projections): FP64 shuffle tree in every warp, FP64 sum of the
@@ -1012,14 +1039,13 @@ static __device__ float v_drift(const float* V, int ldv, int C, Scratch* sc) {
         s = warp_sum(s);
         mx = fmaxf(mx, fabsf(s - 1.f));
     }
-    double m[1] = {0.0};
-    // max via the sum machinery: reduce max per warp through shared memory
-    if (lane == 0) sc->red[warp] = mx;
+    // max of the warp maxima through shared memory (as floats: no FP64 conversions per thread)
+    float* fr = reinterpret_cast<float*>(sc->red);
+    if (lane == 0) fr[warp] = mx;
     __syncthreads();
     float r = 0.f;
-    for (int w = 0; w < NW; ++w) r = fmaxf(r, (float)sc->red[w]);
+    for (int w = 0; w < NW; ++w) r = fmaxf(r, fr[w]);
     __syncthreads();
-    (void)m;
     return r;
 }
 

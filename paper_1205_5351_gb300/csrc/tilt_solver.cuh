@@ -6,6 +6,12 @@
 
 namespace tilt {
 
+// Float scalars of one inner iteration, computed once by thread 0 in FP64 and read by all
+// threads from shared memory (Scratch::fs).
+enum { FS_IMU = 0, FS_THR = 1, FS_MU = 2, FS_IMUN = 3, FS_CC = 8 };
+// Loop control word (Scratch::iscal[5]) set by thread 0 at the end of an iteration.
+enum { LOOP_GO = 0, LOOP_CONVERGED = 1, LOOP_BAD = 2, LOOP_CANCELLED = 3 };
+
 struct InnerOut {
     int iters, sweeps, warm, rank;
     bool converged, bad, cancelled;
@@ -125,13 +131,19 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
     if (threadIdx.x == 0) cyc->cyc_elem += clk() - t0;
 
     const double d0 = sc->scal[1] > 0.0 ? sc->scal[1] : 1.0;
-    double mu = mu0;
+    // thread 0 keeps mu and every FP64 scalar; the others read floats from sc->fs
+    if (threadIdx.x == 0) {
+        sc->scal[12] = mu0;
+        sc->fs[FS_IMU] = (float)(1.0 / mu0);
+        sc->fs[FS_THR] = (float)(lam / mu0);
+        sc->iscal[6] = prm.eps_svd < 0.0 || sc->scal[5] < prm.eps_svd * prm.eps_svd * sc->scal[6];
+    }
+    __syncthreads();
     for (int k = 1; k <= prm.max_inner; ++k) {
         out.iters = k;
         // ---- a6: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate)
         t0 = clk();
-        const double dM2 = sc->scal[5], M2 = sc->scal[6];
-        bool warm = haveV && (prm.eps_svd < 0.0 || dM2 < prm.eps_svd * prm.eps_svd * M2);
+        bool warm = haveV && sc->iscal[6];
         if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
         if (warm) {
             gemm_TV(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
@@ -144,7 +156,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                                       jsched_width(jsched), jsched_order(jsched));
         haveV = true;
         out.sweeps += sw;
-        const float eps = (float)(1.0 / mu);
+        const float eps = sc->fs[FS_IMU];
         svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
         unsigned long long t1 = clk();
         if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
@@ -197,18 +209,16 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                     }
                 }
             }
-            double dacc[1 + PMAX];
-#pragma unroll
-            for (int k2 = 0; k2 < 1 + PMAX; ++k2) dacc[k2] = acc[k2];
-            block_sum<1 + PMAX>(dacc, sc->red);
+            block_sum_f<1 + PMAX>(acc, sc->red);
             if (threadIdx.x == 0) {
-                sc->scal[7] = dacc[0];
+                sc->scal[7] = block_total(sc->red, 0);
                 double v[PMAX];
                 for (int k2 = 0; k2 < p; ++k2) {
-                    sc->ja[k2] = dacc[1 + k2];
+                    sc->ja[k2] = block_total(sc->red, 1 + k2);
                     v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
                 }
                 ginv_apply(sc, p, v, sc->cvec);                       // c'
+                for (int k2 = 0; k2 < PMAX; ++k2) sc->fs[FS_CC + k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
             }
             __syncthreads();
         }
@@ -216,12 +226,12 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         if (threadIdx.x == 0) cyc->cyc_recon += t2 - t1;
 
         // ---- a8: E' = T_{lam/mu}(E - Y/mu - W^T W (A' + E - D_hat)); ||E' - E||^2; J^T E'; ||E'||_1
-        const float imu = (float)(1.0 / mu);
-        const float thr = (float)(lam / mu);
+        const float imu = sc->fs[FS_IMU];
+        const float thr = sc->fs[FS_THR];
         {
             float cc[PMAX];
 #pragma unroll
-            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = sc->fs[FS_CC + k2];
             float acc[2 + PMAX];
 #pragma unroll
             for (int k2 = 0; k2 < 2 + PMAX; ++k2) acc[k2] = 0.f;
@@ -244,35 +254,39 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
 #pragma unroll
                 for (int k2 = 0; k2 < PMAX; ++k2) acc[2 + k2] = fmaf(jv[k2], en, acc[2 + k2]);
             }
-            double dacc[2 + PMAX];
-#pragma unroll
-            for (int k2 = 0; k2 < 2 + PMAX; ++k2) dacc[k2] = acc[k2];
-            block_sum<2 + PMAX>(dacc, sc->red);
+            block_sum_f<2 + PMAX>(acc, sc->red);
             if (threadIdx.x == 0) {
-                sc->scal[8] = dacc[0];
-                sc->scal[9] = dacc[1];
+                sc->scal[8] = block_total(sc->red, 0);
+                sc->scal[9] = block_total(sc->red, 1);
                 double v[PMAX];
                 for (int k2 = 0; k2 < p; ++k2) {
-                    sc->je[k2] = dacc[2 + k2];
+                    sc->je[k2] = block_total(sc->red, 2 + k2);
                     v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
                 }
                 ginv_apply(sc, p, v, sc->cvec);                       // c'' (= dtau at exit)
+                for (int k2 = 0; k2 < PMAX; ++k2) sc->fs[FS_CC + k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
+                // Cond2 and the penalty update (Eqs. rho, mu)
+                const double mu = sc->scal[12];
+                const double dA = sqrt(sc->scal[7]), dE = sqrt(sc->scal[8]);
+                const double c2 = mu * fmax(dA, dE) / d0;
+                const double rho = (c2 < prm.eps2) ? prm.rho0 : 1.0;
+                const double mu_next = fmin(prm.mu_max, rho * mu);
+                sc->scal[13] = mu_next;
+                sc->scal[14] = c2;
+                sc->fs[FS_MU] = (float)mu;
+                sc->fs[FS_IMUN] = (float)(1.0 / mu_next);
             }
             __syncthreads();
         }
-        const double dA = sqrt(sc->scal[7]), dE = sqrt(sc->scal[8]);
         out.l1 = sc->scal[9];
-        const double c2 = mu * fmax(dA, dE) / d0;
-        const double rho = (c2 < prm.eps2) ? prm.rho0 : 1.0;
-        const double mu_next = fmin(prm.mu_max, rho * mu);
 
         // ---- a9: P'' = W^T W (A' + E' - D_hat); Y' = Y + mu P''; next M = A' - Y'/mu_next - P''
         {
             float cc[PMAX];
 #pragma unroll
-            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
-            const float muf = (float)mu;
-            const float imun = (float)(1.0 / mu_next);
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = sc->fs[FS_CC + k2];
+            const float muf = sc->fs[FS_MU];
+            const float imun = sc->fs[FS_IMUN];
             float acc[3] = {0.f, 0.f, 0.f};
             for (int e = threadIdx.x; e < S; e += NT) {
                 float jc = 0.f;
@@ -293,34 +307,45 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                 acc[2] = fmaf(mv, mv, acc[2]);
                 Mp[e] = mv;
             }
-            double dacc[3] = {acc[0], acc[1], acc[2]};
-            block_sum<3>(dacc, sc->red);
+            block_sum_f<3>(acc, sc->red);
             if (threadIdx.x == 0) {
-                sc->scal[10] = dacc[0];
-                sc->scal[5] = dacc[1];
-                sc->scal[6] = dacc[2];
-                sc->iscal[7] = cancel_requested(cancel);
+                sc->scal[10] = block_total(sc->red, 0);
+                sc->scal[5] = block_total(sc->red, 1);
+                sc->scal[6] = block_total(sc->red, 2);
+                // Cond1, the stopping decision, and the scalars of the next iteration
+                const double c1 = sqrt(sc->scal[10]) / d0, c2 = sc->scal[14];
+                const double mu_next = sc->scal[13];
+                sc->scal[15] = c1;
+                int ctl = LOOP_GO;
+                if (!isfinite(c1) || !isfinite(c2)) ctl = LOOP_BAD;
+                else if (cancel_requested(cancel)) ctl = LOOP_CANCELLED;   // the context is being destroyed
+                else if (c1 < prm.eps1 && c2 < prm.eps2) ctl = LOOP_CONVERGED;
+                sc->iscal[5] = ctl;
+                sc->scal[16] = sc->scal[12];      // the mu of this iteration
+                sc->scal[12] = mu_next;
+                sc->fs[FS_IMU] = (float)(1.0 / mu_next);
+                sc->fs[FS_THR] = (float)(lam / mu_next);
+                sc->iscal[6] = prm.eps_svd < 0.0 || sc->scal[5] < prm.eps_svd * prm.eps_svd * sc->scal[6];
             }
             __syncthreads();
         }
         if (threadIdx.x == 0) cyc->cyc_elem += clk() - t2;
-        const double c1 = sqrt(sc->scal[10]) / d0;
-        out.c1 = c1;
-        out.c2 = c2;
-        out.mu_last = mu;
-        if (!isfinite(c1) || !isfinite(c2)) {
+        const int ctl = sc->iscal[5];
+        out.c1 = sc->scal[15];
+        out.c2 = sc->scal[14];
+        out.mu_last = sc->scal[16];
+        if (ctl == LOOP_BAD) {
             out.bad = true;
             break;
         }
-        if (sc->iscal[7]) {          // the context is being destroyed: stop after this iteration
+        if (ctl == LOOP_CANCELLED) {
             out.cancelled = true;
             break;
         }
-        if (c1 < prm.eps1 && c2 < prm.eps2) {
+        if (ctl == LOOP_CONVERGED) {
             out.converged = true;
             break;
         }
-        mu = mu_next;
     }
     return out;
 }
