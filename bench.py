@@ -339,6 +339,9 @@ def run_ours(args, rank, world, local_rank, dist):
             "status_counts": {str(s): sum(1 for r in results if r["status"] == s)
                               for s in sorted({r["status"] for r in results})},
             "inner_iters_per_patch": inner / len(results),
+            # SM cycles per inner iteration over the whole batch: per-iteration cost, unaffected
+            # by which patch happens to finish last
+            "kcycles_per_inner_iter": round(sum(sum(r["phase_cycles"]) for r in results) / max(1, inner) / 1e3, 2),
             "svd": {"sweeps_per_svd": sum(r["svd_sweeps"] for r in results) / max(1, inner),
                     "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner)},
             "phase_split": dict(zip(["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"],

@@ -231,7 +231,7 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.y = take(S);
     L.p = take(S);
     L.mp = take(S);
-    L.zg = take((size_t)d.C * d.C * sizeof(float));
+    L.zg = take((size_t)d.C * d.Cp * sizeof(float));
     // SVD buffers in shared memory as far as they fit, B first (every dot product reads it),
     // then V, then T (bit 0 B, bit 1 V, bit 2 T); the others in the workspace
     const size_t head = smem_head_bytes();
@@ -251,7 +251,7 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     // the C x C SVT coefficients too, where they fit without changing the occupancy class
     // (bit 3); else they stay in the workspace
     {
-        const size_t nz = (size_t)d.C * d.C * sizeof(float);
+        const size_t nz = (size_t)d.C * d.Cp * sizeof(float);
         const size_t lim = L.minb == 2 ? (size_t)100 * 1024 : ctx->max_smem;
         if (place && L.smem + nz <= lim) {
             L.smem_svd |= 8;
@@ -1036,7 +1036,7 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
     a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-    const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.C + 63) & ~(size_t)63;
+    const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
     const size_t need = sizeof(float) * (2 * S4 + nz + (a.smem_svd ? 0 : (2 * nb + nv)));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;

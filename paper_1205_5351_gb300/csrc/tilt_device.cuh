@@ -50,7 +50,7 @@ struct Planes {
     float* Bg;     // ldb * Cp  (SVD work, global mode only)
     float* Vg;     // ldv * Cp
     float* Tg;     // ldb * Cp
-    float* Zg;     // C * C    (X^T b_k of the kept columns, for the reconstruction)
+    float* Zg;     // C * Cp   (X^T b_k of the kept columns, for the reconstruction; rows at stride Cp)
 };
 
 // One problem as the solver kernel sees it.
@@ -955,17 +955,22 @@ static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, con
     __syncthreads();
 }
 
-// The same coefficients as a register-tiled product (inside the solver): each thread owns a
-// 2 x 2 tile of Z (two kept columns of B times two columns of X) and runs over the rows in
-// float4 steps, so every shared-memory load feeds four FMAs.  Consecutive threads take
-// consecutive column pairs of X with the same kept pair (the B loads are broadcasts).
-// Padding rows (R..ldx) of X and B are zero.
+// The same coefficients as a register-tiled product (inside the solver; rows of Z at stride
+// ldz, a multiple of 4): a group of 8 lanes
+// owns a 2 x 2 tile of Z (two kept columns of B times two columns of X); lane g takes the
+// float4 row chunks g, g+8, ... of the four columns (consecutive chunks within a quarter
+// warp: no bank conflicts whatever the column stride), so every shared-memory load feeds
+// four FMAs, and the four sums reduce over 3 shuffle levels.  Padding rows (R..ldx) of X
+// and B are zero.
 static __device__ void svt_coeffs_tiled(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb,
                                         int R, int C, const float* sigma, const float* w, const int* kept, int nk,
-                                        float* __restrict__ Z) {
+                                        float* __restrict__ Z, int ldz) {
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 3, g = lane & 7;
+    const unsigned gmask = 0xFFu << (lane & 24);
+    constexpr int NG = NT / 8;
     const int nq2 = (nk + 1) >> 1, nc2 = (C + 1) >> 1;
     const int nr4 = (R + 3) >> 2;
-    for (int t = threadIdx.x; t < nq2 * nc2; t += NT) {
+    for (int t = grp; t < nq2 * nc2; t += NG) {
         const int qp = t / nc2, cp = t - qp * nc2;
         const int q0 = 2 * qp, q1 = min(q0 + 1, nk - 1);
         const int c0 = 2 * cp, c1 = min(c0 + 1, C - 1);
@@ -975,19 +980,28 @@ static __device__ void svt_coeffs_tiled(const float* __restrict__ X, int ldx, co
         const float4* x0 = reinterpret_cast<const float4*>(X + (size_t)c0 * ldx);
         const float4* x1 = reinterpret_cast<const float4*>(X + (size_t)c1 * ldx);
         float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-        for (int r = 0; r < nr4; ++r) {
+        for (int r = g; r < nr4; r += 8) {
             const float4 u0 = b0[r], u1 = b1[r], v0 = x0[r], v1 = x1[r];
             s00 = fmaf(u0.x, v0.x, fmaf(u0.y, v0.y, fmaf(u0.z, v0.z, fmaf(u0.w, v0.w, s00))));
             s01 = fmaf(u0.x, v1.x, fmaf(u0.y, v1.y, fmaf(u0.z, v1.z, fmaf(u0.w, v1.w, s01))));
             s10 = fmaf(u1.x, v0.x, fmaf(u1.y, v0.y, fmaf(u1.z, v0.z, fmaf(u1.w, v0.w, s10))));
             s11 = fmaf(u1.x, v1.x, fmaf(u1.y, v1.y, fmaf(u1.z, v1.z, fmaf(u1.w, v1.w, s11))));
         }
-        const float f0 = w[k0] / (sigma[k0] * sigma[k0]), f1 = w[k1] / (sigma[k1] * sigma[k1]);
-        Z[(size_t)q0 * C + c0] = s00 * f0;
-        if (c1 != c0) Z[(size_t)q0 * C + c1] = s01 * f0;
-        if (q1 != q0) {
-            Z[(size_t)q1 * C + c0] = s10 * f1;
-            if (c1 != c0) Z[(size_t)q1 * C + c1] = s11 * f1;
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+            s00 += __shfl_xor_sync(gmask, s00, off, 8);
+            s01 += __shfl_xor_sync(gmask, s01, off, 8);
+            s10 += __shfl_xor_sync(gmask, s10, off, 8);
+            s11 += __shfl_xor_sync(gmask, s11, off, 8);
+        }
+        if (g == 0) {
+            const float f0 = w[k0] / (sigma[k0] * sigma[k0]), f1 = w[k1] / (sigma[k1] * sigma[k1]);
+            Z[(size_t)q0 * ldz + c0] = s00 * f0;
+            if (c1 != c0) Z[(size_t)q0 * ldz + c1] = s01 * f0;
+            if (q1 != q0) {
+                Z[(size_t)q1 * ldz + c0] = s10 * f1;
+                if (c1 != c0) Z[(size_t)q1 * ldz + c1] = s11 * f1;
+            }
         }
     }
     __syncthreads();

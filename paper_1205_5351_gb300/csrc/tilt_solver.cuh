@@ -22,7 +22,7 @@ struct SvdBufs {
     float* B;
     float* V;
     float* T;
-    float* Z;   // global, C * C
+    float* Z;   // C x Cp SVT coefficients (shared memory where they fit, else global)
 };
 
 __device__ inline unsigned long long clk() { return clock64(); }
@@ -165,48 +165,39 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         const int nk = sc->iscal[1];
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
-        svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z);
+        svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp);
         {
             float acc[1 + PMAX];
 #pragma unroll
             for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
-            // four consecutive rows of two columns per thread: a float4 of B feeds eight FMAs;
-            // consecutive threads take consecutive row quads (the Z loads are broadcasts)
-            const int nq = (R + 3) >> 2, nc2 = (C + 1) >> 1;
-            for (int idx = threadIdx.x; idx < nq * nc2; idx += NT) {
-                const int cp = idx / nq, r0 = (idx - cp * nq) * 4;
-                const int c0 = 2 * cp, c1 = min(c0 + 1, C - 1);
-                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
+            // one row of four columns per thread: consecutive threads take consecutive rows (the
+            // B loads and the A, J accesses are coalesced), a float4 of Z (rows at stride Cp,
+            // a broadcast) feeds four FMAs
+            const int nc4 = Cp >> 2;
+            for (int idx = threadIdx.x; idx < R * nc4; idx += NT) {
+                const int c4 = idx / R, r = idx - c4 * R;
+                const int c0 = 4 * c4;
+                float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int q = 0; q < nk; ++q) {
-                    const float4 b4 = *reinterpret_cast<const float4*>(buf.B + (size_t)L.kept[q] * ldb + r0);
-                    const float z0 = buf.Z[(size_t)q * C + c0], z1 = buf.Z[(size_t)q * C + c1];
-                    s0.x = fmaf(b4.x, z0, s0.x);
-                    s0.y = fmaf(b4.y, z0, s0.y);
-                    s0.z = fmaf(b4.z, z0, s0.z);
-                    s0.w = fmaf(b4.w, z0, s0.w);
-                    s1.x = fmaf(b4.x, z1, s1.x);
-                    s1.y = fmaf(b4.y, z1, s1.y);
-                    s1.z = fmaf(b4.z, z1, s1.z);
-                    s1.w = fmaf(b4.w, z1, s1.w);
+                    const float b = buf.B[(size_t)L.kept[q] * ldb + r];
+                    const float4 z = *reinterpret_cast<const float4*>(buf.Z + (size_t)q * Cp + c0);
+                    s.x = fmaf(b, z.x, s.x);
+                    s.y = fmaf(b, z.y, s.y);
+                    s.z = fmaf(b, z.z, s.z);
+                    s.w = fmaf(b, z.w, s.w);
                 }
+                const float sv[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (h == 1 && c1 == c0) break;
-                    const int c = h ? c1 : c0;
-                    const float4 s4 = h ? s1 : s0;
-                    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                for (int u = 0; u < 4; ++u) {
+                    if (c0 + u >= C) break;
+                    const int e = (c0 + u) * R + r;
+                    const float sa = sv[u];
+                    const float da = sa - A[e];
+                    acc[0] = fmaf(da, da, acc[0]);
+                    A[e] = sa;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (r0 + u >= R) break;
-                        const int e = c * R + r0 + u;
-                        const float sa = sv[u];
-                        const float da = sa - A[e];
-                        acc[0] = fmaf(da, da, acc[0]);
-                        A[e] = sa;
-#pragma unroll
-                        for (int k2 = 0; k2 < PMAX; ++k2)
-                            if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
-                    }
+                    for (int k2 = 0; k2 < PMAX; ++k2)
+                        if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
                 }
             }
             block_sum_f<1 + PMAX>(acc, sc->red);
