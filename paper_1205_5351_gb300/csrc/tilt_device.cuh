@@ -892,25 +892,39 @@ static __device__ void svt_weights(const float* B, int ldb, int R, int C, float 
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        // kept columns in ascending order (ballot and prefix count), sum and max of
+        // (sigma - eps)_+ over them, then the numerical rank at 1e-3 of the largest
         int nk = 0;
-        double nuc = 0.0, mx = 0.0;
-        for (int k = 0; k < C; ++k) {
-            if (w[k] > 0.f) {
-                kept[nk++] = k;
-                const double sv = (double)sigma[k] - (double)eps;
+        float nuc = 0.f, mx = 0.f;
+        for (int k0 = 0; k0 < C; k0 += 32) {
+            const int k = k0 + lane;
+            const bool keep = k < C && w[k] > 0.f;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                kept[nk + __popc(m & ((1u << lane) - 1u))] = k;
+                const float sv = sigma[k] - eps;
                 nuc += sv;
-                mx = fmax(mx, sv);
+                mx = fmaxf(mx, sv);
             }
+            nk += __popc(m);
         }
-        sc->iscal[1] = nk;
-        sc->scal[3] = nuc;
-        sc->scal[4] = mx;
-        // numerical rank at 1e-3 of the largest kept value
+        nuc = warp_sum(nuc);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        __syncwarp();
         int rk = 0;
-        for (int q = 0; q < nk; ++q)
-            if ((double)sigma[kept[q]] - (double)eps > 1e-3 * mx) ++rk;
-        sc->iscal[2] = rk;
+        for (int q0 = 0; q0 < nk; q0 += 32) {
+            const int q = q0 + lane;
+            const bool big = q < nk && sigma[kept[q]] - eps > 1e-3f * mx;
+            rk += __popc(__ballot_sync(0xffffffffu, big));
+        }
+        if (lane == 0) {
+            sc->iscal[1] = nk;
+            sc->scal[3] = (double)nuc;
+            sc->scal[4] = (double)mx;
+            sc->iscal[2] = rk;
+        }
     }
     __syncthreads();
 }
@@ -1007,36 +1021,49 @@ static __device__ void svt_coeffs_tiled(const float* __restrict__ X, int ldx, co
     __syncthreads();
 }
 
-// B = T V (R x C times C x C), 4 x 4 register tiles; T, B stride ldb (multiple of 4),
-// V stride ldv.  Works on padded sizes (ldb rows, Cp columns).
-static __device__ void gemm_TV(const float* __restrict__ T, int ldb, const float* __restrict__ V, int ldv, float* __restrict__ B,
-                        int Cp, int C) {
-    const int rt_n = ldb / 4, ct_n = Cp / 4;
+// B = T V (R x C times C x C), RT x 4 register tiles (RT = 4 or 8 rows: float4 reads of T,
+// broadcast reads of V); T, B stride ldb (multiple of 4), V stride ldv.  Works on padded
+// sizes (ldb rows, Cp columns).
+template <int RT>
+static __device__ void gemm_TV(const float* __restrict__ T, int ldb, const float* __restrict__ V, int ldv,
+                               float* __restrict__ B, int Cp, int C) {
+    static_assert(RT == 4 || RT == 8, "row tile");
+    const int rt_n = (ldb + RT - 1) / RT, ct_n = Cp / 4;
     const int ntile = rt_n * ct_n;
     for (int t = threadIdx.x; t < ntile; t += NT) {
         const int rt = t % rt_n, ct = t / rt_n;
-        const int r0 = rt * 4, c0 = ct * 4;
-        float acc[4][4];
+        const int r0 = rt * RT, c0 = ct * 4;
+        const bool two = RT == 8 && r0 + 4 < ldb;     // second float4 of rows in range
+        float acc[RT][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < RT; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
         for (int j = 0; j < C; ++j) {
-            const float4 tv = *reinterpret_cast<const float4*>(T + (size_t)j * ldb + r0);
+            float tv[RT];
+            const float4 t0 = *reinterpret_cast<const float4*>(T + (size_t)j * ldb + r0);
+            tv[0] = t0.x; tv[1] = t0.y; tv[2] = t0.z; tv[3] = t0.w;
+            if (RT == 8) {
+                const float4 t1 = two ? *reinterpret_cast<const float4*>(T + (size_t)j * ldb + r0 + 4)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                tv[RT - 4] = t1.x; tv[RT - 3] = t1.y; tv[RT - 2] = t1.z; tv[RT - 1] = t1.w;
+            }
             float vv[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) vv[b] = V[(size_t)(c0 + b) * ldv + j];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                acc[0][b] = fmaf(tv.x, vv[b], acc[0][b]);
-                acc[1][b] = fmaf(tv.y, vv[b], acc[1][b]);
-                acc[2][b] = fmaf(tv.z, vv[b], acc[2][b]);
-                acc[3][b] = fmaf(tv.w, vv[b], acc[3][b]);
-            }
+            for (int a = 0; a < RT; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(tv[a], vv[b], acc[a][b]);
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            *reinterpret_cast<float4*>(B + (size_t)(c0 + b) * ldb + r0) = make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+        for (int b = 0; b < 4; ++b) {
+            *reinterpret_cast<float4*>(B + (size_t)(c0 + b) * ldb + r0) =
+                make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+            if (RT == 8 && two)
+                *reinterpret_cast<float4*>(B + (size_t)(c0 + b) * ldb + r0 + 4) =
+                    make_float4(acc[RT - 4][b], acc[RT - 3][b], acc[RT - 2][b], acc[RT - 1][b]);
+        }
     }
     __syncthreads();
 }

@@ -146,7 +146,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         bool warm = haveV && sc->iscal[6];
         if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
         if (warm) {
-            gemm_TV(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
+            gemm_TV<NCH >= 4 ? 8 : 4>(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
             out.warm++;
         } else {
             for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
