@@ -62,9 +62,9 @@ MAX_SM_MHZ = 2070.0
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
 # sources they were taken on: when the SHA-256 of csrc/ and include/ differs, traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "9e2c6a960b185d1095093c5cb7e192b68c42c65aee5e7914a98b74ab04c7947a",
-               "bytes": {"affine/1024/0": 13637756160 + 17846582272,
-                         "affine/1024/1": 10106382592 + 14146849280}}
+NCU_TRAFFIC = {"sources_sha256": "1d284a54383a170e3dd5df0d039d113dd576dfdc4e64dd5ac0703205f9151d00",
+               "bytes": {"affine/1024/0": 5549559808 + 6370130432,
+                         "affine/1024/1": 6408898816 + 6173202944}}
 
 
 def kernel_sources_sha256() -> str:
