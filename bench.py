@@ -501,11 +501,13 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[wl][0], "patches_per_gpu": args.patches or WORKLOADS[wl][1], "p": 6},
+            "config": {"workload": WORKLOADS[wl][0], "patches_per_gpu": args.patches or WORKLOADS[wl][1],
+                       "p": 8 if wl == "projective" else 6},
             "cpu_baseline": {"value": v, "unit": "patches/s", "cores": cores, "kind": "oracle",
                              "cpu": cpu_model(),
-                             "sample": f"each step: patches of the same workload for about {budget:.0f} s, "
-                                       f"one per process ({n_all} patches total)"},
+                             "sample": f"each step: the next {4 * cores} patches of the same workload (fewer if "
+                                       f"{budget:.0f} s pass first), one per process; {n_all} patches in "
+                                       f"{t_all:.1f} s"},
             "e2e": {"value": v, "unit": "patches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
