@@ -116,6 +116,7 @@ struct Ticket {
     int m = 0, n = 0, p = 0;
     double t_submit = 0, t_done = 0;
     int batch = -1;              // owning grouped launch (order-array lifetime)
+    int klass = -1;              // its occupancy class in that launch
     Request req;
     bool reaped = false;         // finished; result and planes moved to host, device memory released
     Result res{};
@@ -452,7 +453,7 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->phase_cycles[2] = r.cyc_recon;
     out->phase_cycles[3] = r.cyc_elem;
     out->phase_cycles[4] = r.cyc_other;
-    out->launch_class = t.batch < 0 ? -1 : launch_class_of(t.lay);
+    out->launch_class = t.batch < 0 ? -1 : t.klass;
 }
 
 // Copy a device plane (long-side-contiguous) to a host m x n row-major array.
@@ -657,6 +658,11 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
     for (int q = 0; q < count; ++q) idx[q] = q;
     std::vector<int> klass(count);
     for (int q = 0; q < count; ++q) klass[q] = launch_class_of(ts[q].lay);
+    // a batch that does not fill the SMs gains nothing from two CTAs per SM: give every problem
+    // the 128-register kernel (no spills, longer register-resident columns)
+    if (count <= ctx->num_sms)
+        for (int q = 0; q < count; ++q)
+            if (klass[q] == 0) klass[q] = 1;
     auto cls = [&](int q) { return klass[q]; };
     auto cost = [&](int q) {
         const Dims d = make_dims(ts[q].m, ts[q].n, ts[q].p);
@@ -690,6 +696,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         t.slot = ctx->free_slots.back();
         ctx->free_slots.pop_back();
         t.batch = bid;
+        t.klass = klass[q];
         t.t_submit = t0;
         ids[q] = ctx->next_ticket++;
     }
