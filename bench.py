@@ -62,9 +62,9 @@ MAX_SM_MHZ = 2070.0
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
 # sources they were taken on: when the SHA-256 of csrc/ and include/ differs, traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "1d284a54383a170e3dd5df0d039d113dd576dfdc4e64dd5ac0703205f9151d00",
-               "bytes": {"affine/1024/0": 5549559808 + 6370130432,
-                         "affine/1024/1": 6408898816 + 6173202944}}
+NCU_TRAFFIC = {"sources_sha256": "033a5944fcf436ecda1c2200e3e3d818287b5004ead16cd951ac960b25f35022",
+               "bytes": {"affine/1024/0": 5640039168 + 6433005312,
+                         "affine/1024/1": 6422315008 + 6147473664}}
 
 
 def kernel_sources_sha256() -> str:

@@ -659,8 +659,9 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
     std::vector<int> klass(count);
     for (int q = 0; q < count; ++q) klass[q] = launch_class_of(ts[q].lay);
     // a batch that does not fill the SMs gains nothing from two CTAs per SM: give every problem
-    // the 128-register kernel (no spills, longer register-resident columns)
-    if (count <= ctx->num_sms)
+    // the 128-register kernel (no spills, longer register-resident columns).  Not for the
+    // autotuner's timing batches, which must run each bucket in the kernel it will use.
+    if (count <= ctx->num_sms && !ctx->force_js)
         for (int q = 0; q < count; ++q)
             if (klass[q] == 0) klass[q] = 1;
     auto cls = [&](int q) { return klass[q]; };

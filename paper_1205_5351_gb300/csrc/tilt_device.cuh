@@ -606,24 +606,6 @@ __device__ inline float4 rot_y(float4 x, float4 y, float s, float r) {
                        y.w + s * fmaf(-r, y.w, x.w));
 }
 
-__device__ inline float group8_sum(float v, unsigned mask) {
-    v += __shfl_xor_sync(mask, v, 1, 8);
-    v += __shfl_xor_sync(mask, v, 2, 8);
-    v += __shfl_xor_sync(mask, v, 4, 8);
-    return v;
-}
-
-// Rotate the V columns i, j (C rows in float4 chunks, nqv chunks).
-__device__ inline void rotate_v(float* V, int ldv, int i, int j, int nqv, int g, float s, float r) {
-    float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
-    float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
-    for (int q = g; q < nqv; q += 8) {
-        const float4 x = vi[q], y = vj[q];
-        vi[q] = rot_x(x, y, s, r);
-        vj[q] = rot_y(x, y, s, r);
-    }
-}
-
 __device__ inline float group_sum(float v, unsigned mask, int gw) {
 #pragma unroll
     for (int off = 1; off < gw; off <<= 1) v += __shfl_xor_sync(mask, v, off, gw);
