@@ -62,12 +62,39 @@ MAX_SM_MHZ = 2070.0
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
 # sources they were taken on: when the SHA-256 of csrc/ and include/ differs, traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "033a5944fcf436ecda1c2200e3e3d818287b5004ead16cd951ac960b25f35022",
+NCU_TRAFFIC = {"sources_sha256": "de9c8c58b6bbd6411c5d232169608c5b883b31f0df84985c807a4b5c7aa5edff",
                "bytes": {"affine/1024/0": 5640039168 + 6433005312,
                          "affine/1024/1": 6422315008 + 6147473664}}
 
 
+def strip_c_comments(src: str) -> str:
+    """C/C++ source without comments and with runs of whitespace collapsed (string and
+    character literals kept as they are)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_sources_sha256() -> str:
+    """SHA-256 of the library's CUDA/C++ sources with comments and layout removed: a change
+    of code invalidates recorded counters, an edit of comments does not."""
     import hashlib
     h = hashlib.sha256()
     dirs = [os.path.join(ROOT, "paper_1205_5351_gb300", "csrc"), os.path.join(ROOT, "include")]
@@ -75,7 +102,7 @@ def kernel_sources_sha256() -> str:
         for f in sorted(os.listdir(d)):
             if f.endswith((".cu", ".cuh", ".h")):
                 h.update(f.encode())
-                h.update(open(os.path.join(d, f), "rb").read())
+                h.update(strip_c_comments(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()
 
 

@@ -105,8 +105,9 @@ typedef struct {
                                  elementwise passes (E, Y, M), other (Gram, ||D||_2)          */
     int launch_class;    /* grouped launch that solved it (tilt_submit_batch): 0 two CTAs per
                             SM, all SVD buffers in shared memory; 1 one CTA per SM, the SVD
-                            buffers in shared memory as far as they fit; 2 one CTA per SM, all
-                            in device memory.  -1: solved by the persistent worker CTAs      */
+                            buffers in shared memory as far as they fit (also class-0-sized
+                            problems of a batch no larger than the SM count); 2 one CTA per
+                            SM, all in device memory.  -1: solved by the persistent workers */
 } tilt_result;
 
 /* Fill *p with the default parameters. */
@@ -140,7 +141,8 @@ typedef struct {
 } tilt_problem;
 
 /* Queue count problems as one grouped launch per size class (problems ordered by cost,
- * largest first, so that the block scheduler balances the load).  Same semantics as
+ * largest first, so that the block scheduler balances the load; a batch of at most one
+ * problem per SM runs every problem one CTA per SM).  Same semantics as
  * count calls of tilt_submit; tickets_out[count] receives the tickets.  Either every
  * problem is admitted or none is (TILT_E_NOMEM / TILT_E_BUSY). */
 int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, int is_device_ptr,
