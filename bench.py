@@ -61,7 +61,8 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grouped launch of the solver
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
-# sources they were taken on: when the SHA-256 of csrc/ and include/ differs, traffic is null.
+# sources they were taken on: when the SHA-256 of csrc/ and include/ (comments removed)
+# differs, traffic is null.
 NCU_TRAFFIC = {"sources_sha256": "de9c8c58b6bbd6411c5d232169608c5b883b31f0df84985c807a4b5c7aa5edff",
                "bytes": {"affine/1024/0": 5640039168 + 6433005312,
                          "affine/1024/1": 6422315008 + 6147473664}}
