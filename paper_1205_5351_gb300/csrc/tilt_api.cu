@@ -158,9 +158,12 @@ struct tilt_ctx {
     uint64_t launches = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    float* stage = nullptr;         // pinned host staging for plane reads (grows on demand)
+    size_t stage_floats = 0;
     StepOut* step_out = nullptr;    // host-mapped
     StepOut* step_out_dev = nullptr;
     cudaEvent_t ev[6] = {};         // start/end events of the last grouped launches (3 classes)
+    cudaEvent_t ev_copy[3] = {};    // end of the image uploads of a grouped submission, per stream
     int ev_used = 0;
     // persistent workers serving single submissions
     int num_sms = 0;
@@ -340,7 +343,7 @@ void release_ticket(tilt_ctx* ctx, uint64_t id) {
     ctx->tickets.erase(it);
 }
 
-int fetch_plane(tilt_ctx* ctx, const float* dev, int m, int n, float* host);
+int fetch_planes(tilt_ctx* ctx, const float* devA, const float* devE, int m, int n, float* A, float* E);
 
 // Move every finished problem's result and planes to host memory and release its device
 // memory and slot, so that waiting requests can be admitted whatever order the caller
@@ -355,9 +358,8 @@ int reap_finished(tilt_ctx* ctx) {
         t.res = ctx->res[t.slot];
         t.A_host.resize((size_t)t.m * t.n);
         t.E_host.resize((size_t)t.m * t.n);
-        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.A, t.m, t.n, t.A_host.data());
-        if (rc) return rc;
-        rc = fetch_plane(ctx, ctx->probs[t.slot].pl.E, t.m, t.n, t.E_host.data());
+        int rc = fetch_planes(ctx, ctx->probs[t.slot].pl.A, ctx->probs[t.slot].pl.E, t.m, t.n, t.A_host.data(),
+                              t.E_host.data());
         if (rc) return rc;
         ctx->pool.release(t.ws_off, t.ws_bytes);
         ctx->free_slots.push_back(t.slot);
@@ -456,17 +458,31 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->launch_class = t.batch < 0 ? -1 : t.klass;
 }
 
-// Copy a device plane (long-side-contiguous) to a host m x n row-major array.
-int fetch_plane(tilt_ctx* ctx, const float* dev, int m, int n, float* host) {
+// Copy the device planes A and E (long-side-contiguous) to host m x n row-major arrays (either
+// may be NULL): both copies go through one pinned staging buffer and one synchronisation.
+int fetch_planes(tilt_ctx* ctx, const float* devA, const float* devE, int m, int n, float* A, float* E) {
     const Dims d = make_dims(m, n, 0);
-    std::vector<float> tmp((size_t)d.S);
-    CUDA_TRY(cudaMemcpyAsync(tmp.data(), dev, sizeof(float) * d.S, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    const size_t S = (size_t)d.S;
+    if (ctx->stage_floats < 2 * S) {
+        if (ctx->stage) CUDA_TRY(cudaFreeHost(ctx->stage));
+        ctx->stage = nullptr;
+        ctx->stage_floats = 0;
+        CUDA_TRY(cudaHostAlloc(&ctx->stage, sizeof(float) * 2 * S, cudaHostAllocDefault));
+        ctx->stage_floats = 2 * S;
+    }
+    if (A) CUDA_TRY(cudaMemcpyAsync(ctx->stage, devA, sizeof(float) * S, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    if (E) CUDA_TRY(cudaMemcpyAsync(ctx->stage + S, devE, sizeof(float) * S, cudaMemcpyDeviceToHost, ctx->copy_stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->copy_stream));
-    if (d.colmajor) {
-        for (int j = 0; j < n; ++j)
-            for (int i = 0; i < m; ++i) host[(size_t)i * n + j] = tmp[(size_t)j * m + i];
-    } else {
-        memcpy(host, tmp.data(), sizeof(float) * d.S);
+    for (int h = 0; h < 2; ++h) {
+        float* host = h ? E : A;
+        if (!host) continue;
+        const float* tmp = ctx->stage + (h ? S : 0);
+        if (d.colmajor) {
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < m; ++i) host[(size_t)i * n + j] = tmp[(size_t)j * m + i];
+        } else {
+            memcpy(host, tmp, sizeof(float) * S);
+        }
     }
     return TILT_OK;
 }
@@ -546,6 +562,7 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->done_dev, ctx->done, 0));
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->step_out_dev, ctx->step_out, 0));
     for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
+    for (auto& e : ctx->ev_copy) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device));
     CUDA_TRY(cudaHostAlloc(&ctx->q_ring, ns * sizeof(int), cudaHostAllocMapped));
     CUDA_TRY(cudaHostAlloc(&ctx->q_ctl, 4 * sizeof(int), cudaHostAllocMapped));
@@ -709,6 +726,11 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         order[q] = t.slot;
         tickets_out[q] = ids[q];
     }
+    // host images: mark the end of the uploads on each stream; the call waits for them (not
+    // for the solves) before returning, so the caller may reuse its buffers at once even
+    // when they are pinned (pageable sources are staged by the driver anyway)
+    if (!is_device_ptr)
+        for (int c = 0; c < 3; ++c) CUDA_TRY(cudaEventRecord(ctx->ev_copy[c], st[c]));
     std::vector<int> ord_slots(count);
     for (int q = 0; q < count; ++q) ord_slots[q] = order[idx[q]];
     int* ord_dev = reinterpret_cast<int*>(ctx->pool_base + boff);
@@ -732,6 +754,8 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         start = end;
     }
     ctx->ev_used = nev;
+    if (!is_device_ptr)
+        for (int c = 0; c < 3; ++c) CUDA_TRY(cudaEventSynchronize(ctx->ev_copy[c]));
     return TILT_OK;
 }
 
@@ -783,12 +807,8 @@ int tilt_poll(tilt_ctx* ctx, uint64_t ticket, tilt_result* out, float* A_out, fl
     std::atomic_thread_fence(std::memory_order_acquire);
     if (t.t_done == 0) t.t_done = now_ms();
     const Result r = ctx->res[t.slot];
-    if (A_out) {
-        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.A, t.m, t.n, A_out);
-        if (rc) return rc;
-    }
-    if (E_out) {
-        int rc = fetch_plane(ctx, ctx->probs[t.slot].pl.E, t.m, t.n, E_out);
+    if (A_out || E_out) {
+        int rc = fetch_planes(ctx, ctx->probs[t.slot].pl.A, ctx->probs[t.slot].pl.E, t.m, t.n, A_out, E_out);
         if (rc) return rc;
     }
     if (out) fill_result(r, t, out);
@@ -931,6 +951,7 @@ int tilt_destroy(tilt_ctx* ctx) {
     for (auto s : ctx->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(ctx->copy_stream);
     for (auto e : ctx->ev) cudaEventDestroy(e);
+    for (auto e : ctx->ev_copy) cudaEventDestroy(e);
     cudaEventDestroy(ctx->worker_done);
     cudaStreamDestroy(ctx->worker_stream);
     cudaFree(ctx->q_head_dev);
@@ -938,6 +959,7 @@ int tilt_destroy(tilt_ctx* ctx) {
     cudaFreeHost(ctx->q_ctl);
     cudaFree(ctx->pool_base);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->stage) cudaFreeHost(ctx->stage);
     cudaFreeHost(ctx->probs);
     cudaFreeHost(ctx->res);
     cudaFreeHost(ctx->done);

@@ -248,6 +248,9 @@ class Context:
         for q, (img, m, n, tau0, ttype) in enumerate(items):
             if on_device:
                 ptr, (H, W), ld = _dptr(img), img.shape, img.stride(0)
+            elif hasattr(img, "data_ptr"):            # a host (e.g. pinned) PyTorch tensor
+                assert not img.is_cuda and img.is_contiguous() and str(img.dtype) == "torch.float32"
+                ptr, (H, W), ld = img.data_ptr(), tuple(img.shape), img.stride(0)
             else:
                 a = np.ascontiguousarray(img, dtype=np.float32)
                 keep.append(a)
