@@ -519,8 +519,9 @@ def run_reference(args, rank, world):
     t_all = 0.0
     n_all = 0
     budget = max(5.0, 120.0 / max(1, args.steps))
+    per_step = args.patches or 4 * cores           # --patches caps each step's sample
     for s in range(args.steps):
-        sample, wall = run_oracle_sample(pool, cores, budget, first=s * 4 * cores, workload=wl)
+        sample, wall = run_oracle_sample(pool, cores, budget, first=s * per_step, max_patches=per_step, workload=wl)
         vals.append(len(sample) / wall)
         t_all += wall
         n_all += len(sample)
@@ -530,11 +531,11 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[wl][0], "patches_per_gpu": args.patches or WORKLOADS[wl][1],
+            "config": {"workload": WORKLOADS[wl][0], "patches_per_gpu": WORKLOADS[wl][1],
                        "p": 8 if wl == "projective" else 6},
             "cpu_baseline": {"value": v, "unit": "patches/s", "cores": cores, "kind": "oracle",
                              "cpu": cpu_model(),
-                             "sample": f"each step: the next {4 * cores} patches of the same workload (fewer if "
+                             "sample": f"each step: the next {per_step} patches of the same workload (fewer if "
                                        f"{budget:.0f} s pass first), one per process; {n_all} patches in "
                                        f"{t_all:.1f} s"},
             "e2e": {"value": v, "unit": "patches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -19,3 +19,20 @@ def test_comment_edits_keep_the_hash_and_code_edits_change_it(tmp_path, monkeypa
     assert bench.kernel_sources_sha256() == h0
     f.write_text("int f(int a) { return a + 2; }\n")
     assert bench.kernel_sources_sha256() != h0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the FP64 oracle on the host cores) on a two-patch sample."""
+    import json
+    import os
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(os.path.dirname(bench.__file__), "bench.py"), "--impl",
+                          "reference", "--steps", "1", "--warmup", "0", "--patches", "2"],
+                         capture_output=True, text=True, timeout=600, check=True)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "patches/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "2 patches" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "patches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
