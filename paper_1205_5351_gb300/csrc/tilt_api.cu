@@ -728,7 +728,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
     }
     // host images: mark the end of the uploads on each stream; the call waits for them (not
     // for the solves) before returning, so the caller may reuse its buffers at once even
-    // when they are pinned (pageable sources are staged by the driver anyway)
+    // when they are pinned (the CUDA runtime stages pageable sources before it returns)
     if (!is_device_ptr)
         for (int c = 0; c < 3; ++c) CUDA_TRY(cudaEventRecord(ctx->ev_copy[c], st[c]));
     std::vector<int> ord_slots(count);
