@@ -394,7 +394,8 @@ def run_ours(args, rank, world, local_rank, dist):
                                                                if r["launch_class"] == dom_class)),
                          "flops_per_launch": dom_flops,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA issue rate)"},
-            "gpu_launches": launches // max(1, args.steps),
+            "gpu_launches": launches,                 # solver launches inside the timed steps
+            "gpu_launches_per_step": launches // max(1, args.steps),
             "autotune_s": round(tune_s, 2),
             "autotune_schedules": {("gw%d%s" % (w & 255, "-block" if w >> 8 else "")): widths.count(w)
                                    for w in sorted(set(widths))},
