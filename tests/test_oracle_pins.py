@@ -106,6 +106,104 @@ def test_bilinear_exact_on_linear_image():
     assert oob.tolist() == [True, True]
 
 
+def _dlt_homography(src_uv, dst_xy):
+    """Projective tau = [h1..h8] that sends four points to four others: the linear system
+    that x (h7 u + h8 v + 1) = h1 u + h2 v + h3 and y (h7 u + h8 v + 1) = h4 u + h5 v + h6
+    give for each correspondence (direct linear transform), solved by LAPACK."""
+    rows, rhs = [], []
+    for (u, v), (x, y) in zip(src_uv, dst_xy):
+        rows.append([u, v, 1, 0, 0, 0, -x * u, -x * v])
+        rhs.append(x)
+        rows.append([0, 0, 0, u, v, 1, -y * u, -y * v])
+        rhs.append(y)
+    return np.linalg.solve(np.array(rows, float), np.array(rhs, float))
+
+
+def test_projective_map_sends_four_points_where_prescribed():
+    # a homography is fixed by four correspondences in general position (R4): the tau that
+    # the direct linear transform finds for arbitrary targets must map the sources onto them
+    rng = np.random.default_rng(20)
+    for trial in range(20):
+        src = np.array([[-40.0, -30.0], [40.0, -30.0], [40.0, 30.0], [-40.0, 30.0]]) + rng.uniform(-5, 5, (4, 2))
+        dst = src * rng.uniform(0.8, 1.2) + rng.uniform(-8, 8, (4, 2)) + np.array([150.0, 120.0])
+        tau = _dlt_homography(src, dst)
+        x, y, _, _ = O.map_points(tau, O.PROJECTIVE, src[:, 0], src[:, 1])
+        np.testing.assert_allclose(np.c_[x, y], dst, rtol=0, atol=1e-9)
+
+
+def test_projective_map_keeps_lines_straight_and_reduces_to_affine():
+    # projective maps send collinear points to collinear points (a property of every
+    # homography, whatever its parameterisation); with h7 = h8 = 0 it is the affine map
+    rng = np.random.default_rng(21)
+    for trial in range(20):
+        tau = np.r_[rng.uniform(0.8, 1.2), rng.uniform(-0.3, 0.3), rng.uniform(50, 150),
+                    rng.uniform(-0.3, 0.3), rng.uniform(0.8, 1.2), rng.uniform(50, 150),
+                    rng.uniform(-2e-3, 2e-3, 2)]
+        p0, d = rng.uniform(-60, 60, 2), rng.standard_normal(2)
+        t = np.array([-1.3, 0.2, 2.7]) * 20.0
+        u, v = p0[0] + t * d[0], p0[1] + t * d[1]
+        x, y, _, _ = O.map_points(tau, O.PROJECTIVE, u, v)
+        cross = (x[1] - x[0]) * (y[2] - y[0]) - (y[1] - y[0]) * (x[2] - x[0])
+        scale = np.hypot(x[1] - x[0], y[1] - y[0]) * np.hypot(x[2] - x[0], y[2] - y[0])
+        assert abs(cross) <= 1e-12 * scale
+        # and the perspective terms do matter: without them the three points move
+        xa, ya, _, _ = O.map_points(np.r_[tau[:6], 0.0, 0.0], O.PROJECTIVE, u, v)
+        xb, yb, _, _ = O.map_points(tau[:6], O.AFFINE, u, v)
+        np.testing.assert_allclose(np.c_[xa, ya], np.c_[xb, yb], rtol=0, atol=1e-12)
+        assert np.abs(np.c_[x, y] - np.c_[xa, ya]).max() > 1e-3
+
+
+def test_projective_warp_of_rendered_canvas_is_the_texture():
+    # a smooth texture rendered onto a canvas through a known homography (the generator
+    # inverts the 3 x 3 matrix) and warped back at that homography gives the texture on the
+    # window grid, up to the error of bilinear interpolation (|T''| h^2 / 8 per axis)
+    tex = lambda u, v: 0.5 + 0.25 * np.sin(0.3 * u + 0.1 * v) + 0.2 * np.cos(0.17 * v)
+    m, n, H, W = 60, 70, 200, 220
+    L = synth.linear_part(14.0, 0.12)
+    cx, cy, persp = 109.5, 99.5, (8e-4, -6e-4)
+    img = synth._render(tex, H, W, L, cx, cy, persp)
+    tau = synth.tau_vector(L, cx, cy, persp, synth.PROJECTIVE)
+    D, _, oob = O.warp(img, tau, O.PROJECTIVE, m, n)
+    U, V = O.window_uv(m, n)
+    assert oob == 0
+    err = np.abs(D - tex(U, V))
+    assert err.max() < 0.01, err.max()
+    # the same check fails when the perspective terms are dropped
+    D0, _, _ = O.warp(img, np.r_[tau[:6], 0.0, 0.0], O.PROJECTIVE, m, n)
+    assert np.abs(D0 - tex(U, V)).max() > 0.1
+
+
+# ------------------------------------------------------------------ outer stopping rule (R8)
+def test_corner_shift_closed_forms():
+    m, n = 31, 45
+    a, b = (n - 1) / 2, (m - 1) / 2
+    for ttype in (O.AFFINE, O.PROJECTIVE):
+        tau = np.r_[1.0, 0.0, 80.0, 0.0, 1.0, 60.0, 0.0, 0.0][:ttype]
+        # a pure translation moves every corner by |t|
+        dt = np.r_[0.0, 0.0, 0.3, 0.0, 0.0, -0.4, 0.0, 0.0][:ttype]
+        assert abs(O.corner_shift(tau, dt, ttype, m, n) - 0.5) < 1e-12
+        # a uniform scaling by s about the window centre moves each corner by (s - 1) |corner|
+        s = 1.02
+        dt = np.r_[s - 1, 0.0, 0.0, 0.0, s - 1, 0.0, 0.0, 0.0][:ttype]
+        assert abs(O.corner_shift(tau, dt, ttype, m, n) - (s - 1) * math.hypot(a, b)) < 1e-12
+
+
+def test_corner_shift_is_largest_displacement_over_the_window():
+    # for affine maps the displacement is affine in (u, v), so its norm (a convex function)
+    # peaks at a corner of the window: the rule must equal the maximum over a dense grid
+    rng = np.random.default_rng(22)
+    m, n = 24, 37
+    U, V = O.window_uv(m, n)
+    for trial in range(50):
+        tau = np.r_[rng.uniform(0.7, 1.3), rng.uniform(-0.3, 0.3), 70.0, rng.uniform(-0.3, 0.3),
+                    rng.uniform(0.7, 1.3), 65.0]
+        dt = rng.standard_normal(6) * np.r_[1e-2, 1e-2, 0.3, 1e-2, 1e-2, 0.3]
+        x0, y0, _, _ = O.map_points(tau, O.AFFINE, U, V)
+        x1, y1, _, _ = O.map_points(tau + dt, O.AFFINE, U, V)
+        brute = np.hypot(x1 - x0, y1 - y0).max()
+        assert abs(O.corner_shift(tau, dt, O.AFFINE, m, n) - brute) <= 1e-12 * max(1.0, brute)
+
+
 def _fd_jacobian(img, tau, ttype, m, n, h):
     cols = []
     for k in range(ttype):
