@@ -56,7 +56,14 @@ typedef struct {
     int device;                 /* CUDA device ordinal                                        */
     size_t hbm_budget_bytes;    /* device workspace pool; 0 -> 25 % of free memory at create  */
     int max_live;               /* problems admitted at once; 0 -> 65536                      */
-    void* cuda_stream;          /* reserved; the context always creates its own streams       */
+    void* cuda_stream;          /* a cudaStream_t, or NULL: the context creates its own streams.
+                                   Non-NULL: grouped launches (all launch classes, one after
+                                   another), image uploads, plane reads and the step entry
+                                   points are issued on this stream, which the context never
+                                   destroys; tilt_destroy waits for it to drain.  The
+                                   persistent workers of tilt_submit always run on a stream of
+                                   the context's own, since they stay resident between
+                                   submissions                                                */
     const char* autotune_cache; /* file of autotuned Jacobi schedules (read at create, written by
                                    tilt_autotune); NULL: tuning lives in the context only     */
 } tilt_config;
@@ -251,7 +258,8 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
  * asynchronous on `stream` (a cudaStream_t; NULL for the legacy default stream): it returns
  * after the launch, and the outputs are ready when the stream reaches that point.
  * Limits: 1 <= m, n <= 256, eps >= 0; anything else returns TILT_E_INVAL and launches
- * nothing.  The first call on a device looks up the scratch array's device address with that
+ * nothing.  Unlike tilt_svt it reports neither the number of Jacobi sweeps nor whether the
+ * sweep cap (60) was reached: the status record it writes stays in the private scratch.  The first call on a device looks up the scratch array's device address with that
  * device current and sets the kernel's shared-memory limit; make that first call before any
  * stream capture.  Every call on a device shares the one scratch array, so calls whose
  * kernels overlap on the GPU (different streams, or host threads) race and corrupt each

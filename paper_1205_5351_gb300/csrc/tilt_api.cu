@@ -140,6 +140,7 @@ struct tilt_ctx {
     size_t max_smem = 0;
     cudaStream_t streams[4] = {};
     cudaStream_t copy_stream = nullptr;
+    bool own_streams = true;        // false: streams[] and copy_stream are the caller's stream
     int next_stream = 0;
     char* pool_base = nullptr;
     Pool pool;
@@ -210,11 +211,11 @@ bool params_ok(const Params& q) {
 std::pair<int, int> size_bucket(int R, int C) { return {(R + 15) / 16, (C + 15) / 16}; }
 
 // Jacobi schedule for an R x C problem: the autotuned one for its size bucket, else the
-// default group width with round-robin ordering.
+// default schedule (block-cyclic ordering).
 int jsched_for(const tilt_ctx* ctx, int R, int C) {
     if (ctx->force_js) return ctx->force_js;
     auto it = ctx->tune.find(size_bucket(R, C));
-    return it != ctx->tune.end() ? it->second : default_group_width(R, C);
+    return it != ctx->tune.end() ? it->second : default_schedule(R, C);
 }
 
 bool jsched_valid(int js) {
@@ -543,8 +544,15 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device));
     ctx->max_smem = (size_t)optin - 2048;    // static shared memory of the solver kernel
     CUDA_TRY(configure_kernels(ctx->max_smem));
-    for (auto& s : ctx->streams) CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    if (cfg->cuda_stream) {
+        // the caller's stream carries every grouped launch, copy and step of this context
+        ctx->own_streams = false;
+        for (auto& s : ctx->streams) s = reinterpret_cast<cudaStream_t>(cfg->cuda_stream);
+        ctx->copy_stream = reinterpret_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        for (auto& s : ctx->streams) CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    }
     size_t freeb = 0, totalb = 0;
     CUDA_TRY(cudaMemGetInfo(&freeb, &totalb));
     size_t budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : freeb / 4;
@@ -879,7 +887,7 @@ int tilt_autotune(tilt_ctx* ctx, const int* shapes, int count, tilt_transform ty
             prm.max_outer = 1;
             prm.max_inner = 30;      // long enough that warm-started SVDs dominate, as in real solves
             prm.eps1 = 0.0;
-            int best = default_group_width(d.R, d.C);
+            int best = default_schedule(d.R, d.C);
             float best_ms = 1e30f;
             const int widths[3] = {4, 8, 16};
             float cand_ms[6];
@@ -948,8 +956,10 @@ int tilt_destroy(tilt_ctx* ctx) {
         if (now_ms() > t_end) return fail(TILT_E_TIMEOUT, "work still running after 120 s; context leaked");
         std::this_thread::sleep_for(std::chrono::milliseconds(1));
     }
-    for (auto s : ctx->streams) cudaStreamDestroy(s);
-    cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->own_streams) {
+        for (auto s : ctx->streams) cudaStreamDestroy(s);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
     for (auto e : ctx->ev) cudaEventDestroy(e);
     for (auto e : ctx->ev_copy) cudaEventDestroy(e);
     cudaEventDestroy(ctx->worker_done);

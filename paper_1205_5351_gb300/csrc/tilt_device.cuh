@@ -856,6 +856,14 @@ constexpr int JSCHED_BLOCK = 256;   // schedule bit: block-cyclic pair ordering
 __host__ __device__ inline int jsched_width(int js) { return js & 255; }
 __host__ __device__ inline int jsched_order(int js) { return js >> 8; }
 
+// Schedule of a size bucket the autotuner has not timed: block-cyclic ordering (one CTA
+// barrier per block round instead of one per round), 16 lanes per pair for the long
+// columns of wide matrices, 8 otherwise.  (The autotuner picks block-cyclic for most
+// buckets; round-robin width 4 was 1.4x slower on 200 x 200 windows.)
+__host__ __device__ inline int default_schedule(int R, int C) {
+    return ((R > 128 && C >= 64) ? 16 : 8) | JSCHED_BLOCK;
+}
+
 // Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the
 // list of kept columns.  Returns (via scal) sum (sigma - eps)_+, max (sigma - eps)_+ and
 // the kept count (iscal[1]).

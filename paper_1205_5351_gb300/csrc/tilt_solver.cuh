@@ -398,6 +398,8 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
     if (threadIdx.x == 0) res.cyc_warp += clk() - t0;
     if (status == -4) {
         // cancelled before it started: tau stays tau0
+    } else if (!isfinite(sc->scal[0])) {
+        status = -1;                                   // a non-finite sample in the window
     } else if (!(sc->scal[0] > 0.0)) {
         status = -3;
     } else {
@@ -412,6 +414,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             t0 = clk();
             if (outer > 1) {
                 k1_warp_jacobian(pr.img, pr.ld, pr.H, pr.W, d, pr.ttype, sc->tau, pr.pl.Dhat, pr.pl.J, sc);
+                if (!isfinite(sc->scal[0])) { status = -1; break; }
                 if (!(sc->scal[0] > 0.0)) { status = -3; break; }
             }
             unsigned long long t1 = clk();

@@ -179,9 +179,12 @@ def jacobian_from_rows(J: np.ndarray, m: int, n: int) -> np.ndarray:
 class Context:
     """One solver context on one device (``tilt_create`` / ``tilt_destroy``)."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_live: int = 0, autotune_cache: str = None):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_live: int = 0, autotune_cache: str = None,
+                 cuda_stream: int = 0):
+        """``cuda_stream``: a cudaStream_t handle (e.g. ``torch.cuda.Stream().cuda_stream``) that
+        carries the context's grouped launches, copies and steps; 0: the context's own streams."""
         self._cache = autotune_cache.encode() if autotune_cache else None
-        cfg = Config(device, hbm_budget_bytes, max_live, None, self._cache)
+        cfg = Config(device, hbm_budget_bytes, max_live, cuda_stream or None, self._cache)
         h = _vp()
         _check(lib().tilt_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h

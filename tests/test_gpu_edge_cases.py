@@ -1,6 +1,7 @@
 """Edge cases of the CUDA path through the C ABI: a window partly outside the image (clamped
 samples, counted as in the oracle), degenerate windows (zero image: status -3; constant image:
-singular J^T J + Q^T Q, status -2), an empty batch, and the largest window size end to end."""
+singular J^T J + Q^T Q, status -2; a non-finite sample: status -1), the caller's stream, an
+empty batch, and the largest window size end to end."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,45 @@ def test_degenerate_windows_report_their_status(T):
     for r in (r1, rb[1]):
         assert r["status"] == -2                       # zero image gradient: J = 0, G = Q^T Q is rank 3
         np.testing.assert_array_equal(r["tau"], tau0)
+
+
+def test_non_finite_window_reports_status_minus_one(T):
+    # a NaN written into the host image inside the window (host-side injection): the warp
+    # sees a non-finite sample, both submit paths retire the problem with status -1 and
+    # keep tau0; a problem in the same batch with a clean image is unaffected
+    p = synth.small_affine(3)
+    bad = p.img.copy()
+    bad[bad.shape[0] // 2, bad.shape[1] // 2] = np.nan
+    prm = T.default_params(max_outer=2)
+    with T.Context(0) as ctx:
+        r0 = ctx.wait(ctx.submit(bad, p.m, p.n, p.tau0, p.ttype, prm), 60000)
+        tk = ctx.submit_batch([(bad, p.m, p.n, p.tau0, p.ttype), (p.img, p.m, p.n, p.tau0, p.ttype)], prm)
+        rb = [ctx.wait(t, 60000) for t in tk]
+    for r in (r0, rb[0]):
+        assert r["status"] == -1
+        np.testing.assert_array_equal(r["tau"], p.tau0)
+    assert rb[1]["status"] >= 0
+    ref = O.tilt(p.img.astype(np.float64), p.tau0, p.ttype, p.m, p.n, O.Params(max_outer=2))
+    assert O.tau_error(rb[1]["tau"], ref.tau) <= 1e-3
+
+
+def test_caller_stream_carries_the_context(T):
+    # tilt_config.cuda_stream: grouped launches, copies and steps on the caller's stream give
+    # the same results as the context's own streams (bit for bit: same kernels, same inputs)
+    patches = [q for q in synth.mixed_affine_batch(12, first=40) if max(q.m, q.n) <= 80][:3]
+    prm = T.default_params(max_outer=2)
+    items = [(q.img, q.m, q.n, q.tau0, q.ttype) for q in patches]
+    with T.Context(0) as ctx:
+        want = [ctx.wait(t, 300000) for t in ctx.submit_batch(items, prm)]
+    st = torch.cuda.Stream()
+    with T.Context(0, cuda_stream=st.cuda_stream) as ctx:
+        got = [ctx.wait(t, 300000) for t in ctx.submit_batch(items, prm)]
+        Dh, J, norm, oob = ctx.warp_jacobian(torch.from_numpy(patches[0].img).cuda(), patches[0].m,
+                                             patches[0].n, patches[0].tau0, 6)
+    for g, w in zip(got, want):
+        np.testing.assert_array_equal(g["tau"], w["tau"])
+        assert g["inner_iters"] == w["inner_iters"]
+    assert norm > 0
 
 
 def test_empty_batch(T):

@@ -131,26 +131,25 @@ def test_one_inner_iteration_parity(T, ctx, seed, m, n, ttype):
     lam = 1 / math.sqrt(max(m, n))
     ref = O.inner_ladmap(Dh, J, Q, lam, Dh, 0 * Dh, 0 * Dh, O.Params(max_inner=1), mu0=mu0)
     assert out["iters"] == 1
-    for name, dev, want in (("A", A_d, ref.A), ("E", E_d, ref.E)):
+    # every result of one iteration at the per-kernel bound: relative Frobenius error <= 1e-5
+    # (measured on these cases: A <= 4.1e-7, E exact, Y <= 1.1e-7, dtau <= 1.7e-6,
+    # c1 and c2 <= 5e-8)
+    for name, dev, want in (("A", A_d, ref.A), ("E", E_d, ref.E), ("Y", Y_d, ref.Yt)):
         got = T.from_long_layout(dev.cpu().numpy(), m, n)
         assert rel(got, want) <= 1e-5, (name, rel(got, want))
-    # Y = mu W^T W (A + E - D_hat) is a difference of O(||D_hat||) FP32 terms: its error
-    # is bounded relative to mu ||D_hat||_F, not to ||Y||
-    Y = T.from_long_layout(Y_d.cpu().numpy(), m, n)
-    assert np.linalg.norm(Y - ref.Yt) <= 1e-5 * mu0 * np.linalg.norm(Dh)
-    # likewise dtau = G^-1 J^T (A + E - D_hat) and c1 = ||W^T W (A + E - D_hat)|| / d0
     dt_ref = O.delta_tau(O.WtW(J, Q), ref.A, ref.E, Dh)
-    G = J.T @ J + Q.T @ Q
-    assert np.linalg.norm(G @ (out["dtau"] - dt_ref)) <= 1e-5 * np.linalg.norm(J, 2) * np.linalg.norm(Dh)
-    assert abs(out["c1"] - ref.c1) <= 1e-5 and abs(out["c2"] - ref.c2) <= 1e-4 * ref.c2
+    assert rel(out["dtau"], dt_ref) <= 1e-5, rel(out["dtau"], dt_ref)
+    assert abs(out["c1"] - ref.c1) <= 1e-5 * ref.c1 and abs(out["c2"] - ref.c2) <= 1e-5 * ref.c2
 
 
 @pytest.mark.parametrize("seed,m,n,ttype", [(51, 50, 50, 6), (52, 64, 45, 8), (53, 120, 110, 6)])
 def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
-    # the whole inner loop to convergence.  The stopping rules (Cond1, Cond2) leave the
-    # iterates within about eps2/mu of the fixed point and FP32 rounding enters every
-    # iteration, so A and E (the split of the unit-norm D_hat) are compared at 1e-3 of
-    # ||D_hat||_F, dtau at 1e-3 relative
+    # the whole inner loop to convergence: the FP32 rounding of every iteration (about
+    # 1e-7 relative, see the one-iteration test) carries into the next over 56-73
+    # iterations, so the converged A, E and dtau are compared at 1e-4 relative (measured:
+    # A <= 2.9e-6, E <= 2.2e-5 relative to ||E|| -- E's small entries sit at the threshold
+    # lam/mu --, dtau <= 1.5e-5), and the iteration counts agree to one (a stopping test that
+    # lands within rounding of its threshold may flip)
     tau, Dh_d, J_d, Dh, J = _inner_inputs(T, ctx, seed, m, n, ttype)
     mu0 = O.default_mu0(Dh)
     A_d, E_d, Y_d = Dh_d.clone(), torch.zeros_like(Dh_d), torch.zeros_like(Dh_d)
@@ -161,13 +160,11 @@ def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
     assert ref.converged
     A = T.from_long_layout(A_d.cpu().numpy(), m, n)
     E = T.from_long_layout(E_d.cpu().numpy(), m, n)
-    nD = np.linalg.norm(Dh)
-    assert np.linalg.norm(A - ref.A) <= 1e-3 * nD and np.linalg.norm(E - ref.E) <= 1e-3 * nD
-    # dtau moves the image by J dtau; A + E - D_hat carries the same displacement, so the
-    # 1e-3 ||D_hat|| bound on A and E bounds J (dtau - dtau_ref) the same way
+    assert rel(A, ref.A) <= 1e-4, rel(A, ref.A)
+    assert rel(E, ref.E) <= 1e-4, rel(E, ref.E)
     dt_ref = O.delta_tau(O.WtW(J, Q), ref.A, ref.E, Dh)
-    assert np.linalg.norm(J @ (out["dtau"] - dt_ref)) <= 1e-3 * nD
-    assert abs(out["iters"] - ref.iters) <= max(2, ref.iters // 10), (out["iters"], ref.iters)
+    assert rel(out["dtau"], dt_ref) <= 1e-4, rel(out["dtau"], dt_ref)
+    assert abs(out["iters"] - ref.iters) <= 1, (out["iters"], ref.iters)
     assert O.numerical_rank(A) == O.numerical_rank(ref.A)
 
 
