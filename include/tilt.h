@@ -94,7 +94,9 @@ typedef struct {
     int status;          /* 0 outer loop converged, 1 max_outer reached, 2 some inner loop hit
                             max_inner (tau still valid), < 0 numeric failure (-1 non-finite,
                             -2 singular J^T J + Q^T Q, -3 zero image window), -4 cancelled
-                            by tilt_destroy (tau = the last completed outer step's)           */
+                            by tilt_destroy (tau = the last completed outer step's), -5 a
+                            bounded device wait expired (a tensor-core product did not
+                            complete; tau = the last completed outer step's)                  */
     int p;               /* 6 or 8                                                             */
     double tau[8];       /* final transform (first p entries)                                 */
     double objective;    /* ||A||_* + lambda ||E||_1 of the last inner loop (Eq. TILT_2)       */

@@ -94,7 +94,7 @@ private:
 
 struct Layout {   // byte offsets inside one problem's workspace
     size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, order, total;
-    int smem_svd, minb, jsched;
+    int smem_svd, minb, jsched, tc_nbuf;
     size_t smem;
 };
 
@@ -237,27 +237,43 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.p = take(S);
     L.mp = take(S);
     L.zg = take((size_t)d.C * d.Cp * sizeof(float));
-    // SVD buffers in shared memory as far as they fit, B first (every dot product reads it),
-    // then V, then T (bit 0 B, bit 1 V, bit 2 T); the others in the workspace
+    // SVD buffers in shared memory as far as they fit next to the stage buffers of the
+    // tensor-core products (two buffers where they fit, else one), B first (every dot
+    // product reads it), then V, then T (bit 0 B, bit 1 V, bit 2 T); the others in the
+    // workspace
     const size_t head = smem_head_bytes();
     const size_t nb = (size_t)d.ldb * d.Cp * sizeof(float), nv = (size_t)d.ldv * d.Cp * sizeof(float);
-    int place = 0;
-    if (2 * nb + nv + head <= ctx->max_smem) place = 7;
-    else if (nb + nv + head <= ctx->max_smem) place = 3;
-    else if (nb + head <= ctx->max_smem) place = 1;
+    const bool tc = use_tc_products(d);
+    const size_t st1 = tc ? tc_stage_for(d, 1) : 0, st2 = tc ? tc_stage_for(d, 2) : 0;
+    const int places[4] = {7, 3, 1, 0};
+    int place = 0, nbuf = 1;
+    for (int pi = 0; pi < 4; ++pi) {
+        const int pl = places[pi];
+        const size_t svd = ((pl & 1) ? nb : 0) + ((pl & 2) ? nv : 0) + ((pl & 4) ? nb : 0);
+        if (head + svd + st2 <= ctx->max_smem) { place = pl; nbuf = 2; break; }
+        if (head + svd + st1 <= ctx->max_smem) { place = pl; nbuf = 1; break; }
+    }
+    const size_t svd_bytes = ((place & 1) ? nb : 0) + ((place & 2) ? nv : 0) + ((place & 4) ? nb : 0);
+    // the 2-CTA kernel keeps R <= 96 columns in registers and needs <= 100 KB of shared
+    // memory per CTA: one stage buffer when two would not fit
+    const size_t lim2 = (size_t)100 * 1024;
+    L.minb = 1;
+    if (place == 7 && d.ldb <= 96) {
+        if (head + svd_bytes + st2 <= lim2) { L.minb = 2; nbuf = 2; }
+        else if (head + svd_bytes + st1 <= lim2) { L.minb = 2; nbuf = 1; }
+    }
     L.smem_svd = place;
-    L.smem = head + ((place & 1) ? nb : 0) + ((place & 2) ? nv : 0) + ((place & 4) ? nb : 0);
+    L.tc_nbuf = tc ? nbuf : 0;
+    L.smem = head + svd_bytes + (nbuf == 2 ? st2 : st1);
     L.bg = (place & 1) ? 0 : take(nb);
     L.vg = (place & 2) ? 0 : take(nv);
     L.tg = (place & 4) ? 0 : take(nb);
     L.jsched = jsched_for(ctx, d.R, d.C);
-    // the 2-CTA kernel keeps R <= 96 columns in registers
-    L.minb = (place == 7 && L.smem <= 100 * 1024 && d.ldb <= 96) ? 2 : 1;
     // the C x C SVT coefficients too, where they fit without changing the occupancy class
     // (bit 3); else they stay in the workspace
     {
         const size_t nz = (size_t)d.C * d.Cp * sizeof(float);
-        const size_t lim = L.minb == 2 ? (size_t)100 * 1024 : ctx->max_smem;
+        const size_t lim = L.minb == 2 ? lim2 : ctx->max_smem;
         if (place && L.smem + nz <= lim) {
             L.smem_svd |= 8;
             L.smem += nz;
@@ -318,6 +334,7 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.pl.Vg = (L.smem_svd & 2) ? nullptr : reinterpret_cast<float*>(base + L.vg);
     pr.pl.Tg = (L.smem_svd & 4) ? nullptr : reinterpret_cast<float*>(base + L.tg);
     pr.smem_svd = L.smem_svd;
+    pr.tc_nbuf = L.tc_nbuf;
     pr.jsched = L.jsched;
     pr.res = ctx->res_dev + t.slot;
     pr.done = ctx->done_dev + t.slot;
@@ -1035,14 +1052,14 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
     if (m < 1 || n < 1 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "matrix %d x %d", m, n);
     if (!(eps >= 0.f)) return fail(TILT_E_INVAL, "eps must be >= 0");
     const Dims d = make_dims(m, n, 0);
-    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
     SvtArgs a{};
     a.M = M_dev;
     a.A = A_dev;
     a.m = m; a.n = n; a.eps = eps;
     a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-    const size_t nz = (size_t)d.C * d.C;
+    const size_t nz = (size_t)d.C * d.Cp;
     const size_t need = sizeof(float) * ((a.smem_svd ? 0 : (2 * nb + nv)) + MAX_SIDE + ((nz + 63) & ~(size_t)63));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
@@ -1058,6 +1075,7 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
     CUDA_TRY(launch_svt_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
     rc = run_step(ctx);
     if (rc) return rc;
+    if (ctx->step_out->status == -5) return fail(TILT_E_TIMEOUT, "a tensor-core product did not complete");
     if (sigma_out) CUDA_TRY(cudaMemcpy(sigma_out, a.sigma, sizeof(float) * d.C, cudaMemcpyDeviceToHost));
     if (sweeps_out) *sweeps_out = ctx->step_out->sweeps;
     return TILT_OK;
@@ -1073,7 +1091,7 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     a.prm = to_params(params);
     if (!params_ok(a.prm)) return fail(TILT_E_INVAL, "parameters out of range");
     const Dims d = make_dims(m, n, (int)type);
-    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
     a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
@@ -1103,6 +1121,7 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     if (rc) return rc;
     const StepOut& o = *ctx->step_out;
     if (o.status == -2) return fail(TILT_E_INVAL, "J^T J + Q^T Q is singular");
+    if (o.status == -5) return fail(TILT_E_TIMEOUT, "a tensor-core product did not complete");
     if (iters_out) *iters_out = o.iters;
     if (dtau_out)
         for (int k = 0; k < (int)type; ++k) dtau_out[k] = o.dtau[k];

@@ -12,6 +12,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "tilt_tc.cuh"
+
 namespace tilt {
 
 constexpr int NT = 512;          // threads per CTA
@@ -63,6 +65,8 @@ struct Problem {
     Params prm;
     Planes pl;
     int smem_svd;          // bits 0-3: B, V, T, Z live in shared memory (else Bg, Vg, Tg, Zg)
+    int tc_nbuf;           // stage buffers of the tensor-core products (1 or 2, after B|V|T|Z);
+                           // 0: the products run on the SIMT pipes
     int jsched;            // Jacobi schedule: bits 0-7 group width (lanes per column pair: 4, 8
                            // or 16), bit 8 block-cyclic pair ordering (else round-robin)
     Result* res;           // host-mapped result record
@@ -102,6 +106,23 @@ __host__ __device__ inline size_t svd_smem_bytes(const Dims& d) {
     return sizeof(float) * ((size_t)2 * d.ldb * d.Cp + (size_t)d.ldv * d.Cp);
 }
 
+// Tensor-core products of the SVD and the SVT: K chunks of TC_KC, accumulators of up to
+// min(C rounded up to 16, TC_NMAX) columns; every CTA holds TC_TMEM_COLS columns of tensor
+// memory (two CTAs per SM at most: 512 columns).
+constexpr int TC_KC = 8;
+constexpr uint32_t TC_TMEM_COLS = 256;
+// Windows whose products run on the tensor cores: below this short side the per-chunk
+// staging and synchronisation of the tensor-core path cost more than the register-tiled
+// SIMT products (measured on the 40-120 px windows of the affine batch: the SVT
+// reconstruction took 15 % more cycles on the tensor cores).
+constexpr int TC_MIN_C = 160;
+__host__ __device__ inline bool use_tc_products(const Dims& d) { return d.C >= TC_MIN_C; }
+__host__ __device__ inline int tc_np(const Dims& d) {
+    const int np = (d.C + 15) & ~15;
+    return np < TC_NMAX ? np : TC_NMAX;
+}
+__host__ __device__ inline size_t tc_stage_for(const Dims& d, int nbuf) { return tc_stage_bytes(tc_np(d), TC_KC, nbuf); }
+
 // ------------------------------------------------------------------------------ CTA scratch
 // Small per-CTA scalars kept in shared memory.
 struct Scratch {
@@ -119,6 +140,7 @@ struct Scratch {
     float fs[16];              // per-iteration float scalars, computed by thread 0 (FS_*)
     int iscal[8];
     int flag[2];
+    TcState tc;                // tensor-core products: mbarriers, tensor-memory address, error
 };
 
 // Dynamic shared memory layout: [Scratch][sigma: C floats][w: C floats][kept: C ints][B|V|T]
@@ -924,10 +946,39 @@ static __device__ void svt_weights(const float* B, int ldb, int R, int C, float 
 //   S_eps(X) = sum_k (sigma_k - eps)_+ u_k v_k^T = sum_k (w_k / sigma_k^2) b_k (X^T b_k)^T,
 // which needs only the measured orthogonality of B, not the orthogonality of the
 // accumulated V (FP32 rotations drift V away from orthogonal far faster than B).
-// Z[q*C + c] = (w_k / sigma_k^2) (X^T b_k)_c for the kept columns k = kept[q].
+// Z[q * ldz + c] = (w_k / sigma_k^2) (X^T b_k)_c for the kept columns k = kept[q]: the
+// product B_K^T X (nk x R times R x C) on the tensor cores (3xTF32, FP32 accumulate).
+// X and B have column stride ldx / ldb (rows R).  All threads; false if a wait gave up.
+static __device__ bool svt_coeffs_tc(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb,
+                                     int R, int C, const float* sigma, const float* w, const int* kept, int nk,
+                                     float* __restrict__ Z, int ldz, unsigned char* stage, int nbuf, TcState* tc) {
+    if (nk <= 0) return true;
+    auto la = [=](int q, int r) { return B[(size_t)kept[q] * ldb + r]; };   // B_K^T: contiguous along R
+    auto lb = [=](int r, int c) { return X[(size_t)c * ldx + r]; };        // X: contiguous along R
+    auto ep = [=](int q, int c, float v) {
+        const int k = kept[q];
+        Z[(size_t)q * ldz + c] = v * (w[k] / (sigma[k] * sigma[k]));
+    };
+    return tc_gemm<NT, true, true>(nk, C, R, la, lb, ep, stage, TC_KC, nbuf, tc);
+}
+
+// Warm start of the Jacobi SVD: B = T V (R x C times C x C, both column-major with strides
+// ldb and ldv) on the tensor cores (3xTF32, FP32 accumulate).  Rows up to ldb are written,
+// so B's padding rows (zero in T) stay zero.  All threads; false if a wait gave up.
+static __device__ bool warm_start_tc(const float* __restrict__ T, int ldb, const float* __restrict__ V, int ldv,
+                                     float* __restrict__ B, int C, unsigned char* stage, int nbuf, TcState* tc) {
+    auto la = [=](int r, int j) { return T[(size_t)j * ldb + r]; };        // contiguous along rows
+    auto lb = [=](int j, int c) { return V[(size_t)c * ldv + j]; };        // contiguous along K
+    auto ep = [=](int r, int c, float v) { B[(size_t)c * ldb + r] = v; };
+    return tc_gemm<NT, false, true>(ldb, C, C, la, lb, ep, stage, TC_KC, nbuf, tc);
+}
+
+// The coefficients Z[q * ldz + c] = (w_k / sigma_k^2) (X^T b_k)_c on the SIMT pipes for any
+// column stride ldx of X (the step entry point reads X in place), one 8-lane group per
+// coefficient.
 static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, const float* __restrict__ B, int ldb, int R,
                                        int C, const float* sigma, const float* w, const int* kept, int nk,
-                                       float* __restrict__ Z) {
+                                       float* __restrict__ Z, int ldz) {
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 3, g = lane & 7;
     const unsigned gmask = 0xFFu << (lane & 24);
     constexpr int NG = NT / 8;
@@ -953,14 +1004,15 @@ static __device__ void svt_left_coeffs(const float* __restrict__ X, int ldx, con
         s += __shfl_xor_sync(gmask, s, 4, 8);
         if (g == 0) {
             const float sg = sigma[k];
-            Z[(size_t)q * C + c] = s * (w[k] / (sg * sg));
+            Z[(size_t)q * ldz + c] = s * (w[k] / (sg * sg));
         }
     }
     __syncthreads();
 }
 
-// The same coefficients as a register-tiled product (inside the solver; rows of Z at stride
-// ldz, a multiple of 4): a group of 8 lanes
+// The same coefficients as a register-tiled FP32 product on the SIMT pipes (the windows too
+// small for the tensor-core product to pay; rows of Z at stride ldz, a multiple of 4): a
+// group of 8 lanes
 // owns a 2 x 2 tile of Z (two kept columns of B times two columns of X); lane g takes the
 // float4 row chunks g, g+8, ... of the four columns (consecutive chunks within a quarter
 // warp: no bank conflicts whatever the column stride), so every shared-memory load feeds

@@ -24,13 +24,16 @@ __global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const 
     __shared__ Problem sp;
     __shared__ Result sres;
     SmemLayout L = carve_smem(smem_raw);
+    constexpr bool TCP = MINB < 2;     // the 2-CTA kernel's windows are all below the tensor-core size
+    if (TCP) tc_setup(&L.sc->tc, TC_TMEM_COLS);
     copy_to_shared(&sp, probs + order[blockIdx.x]);
-    solve_problem<NCH>(sp, L, sres);
+    solve_problem<NCH, TCP>(sp, L, sres);
     if (threadIdx.x == 0) {
         *sp.res = sres;
         __threadfence_system();
         *sp.done = 1;
     }
+    if (TCP) tc_teardown(&L.sc->tc, TC_TMEM_COLS);
 }
 
 __device__ inline int load_acquire_sys(const int* p) {
@@ -50,6 +53,7 @@ __global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue
     __shared__ Result sres;
     __shared__ int claim;
     SmemLayout L = carve_smem(smem_raw);
+    tc_setup(&L.sc->tc, TC_TMEM_COLS);
     for (;;) {
         if (threadIdx.x == 0) {
             int got = -1;
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue
         __syncthreads();
         const int slot = claim;
         __syncthreads();
-        if (slot < 0) return;
+        if (slot < 0) break;
         {   // the descriptor was written by the host before the tail was published
             const volatile int* s = reinterpret_cast<const volatile int*>(probs + slot);
             int* d = reinterpret_cast<int*>(&sp);
@@ -97,6 +101,7 @@ __global__ void __launch_bounds__(NT, 1) worker_kernel(Problem* probs, WorkQueue
         }
         __syncthreads();
     }
+    tc_teardown(&L.sc->tc, TC_TMEM_COLS);
 }
 
 __global__ void __launch_bounds__(NT, 1) warp_step_kernel(WarpArgs a) {
@@ -128,14 +133,18 @@ __global__ void __launch_bounds__(NT, 1) gram_step_kernel(GramArgs a) {
 __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     SmemLayout L = carve_smem(smem_raw);
+    tc_setup(&L.sc->tc, TC_TMEM_COLS);
     const Dims d = make_dims(a.m, a.n, 0);
     float *B, *V;
+    unsigned char* stage;
     if (a.smem_svd) {
         B = L.svd;
         V = B + (size_t)d.ldb * d.Cp;
+        stage = reinterpret_cast<unsigned char*>(V + (size_t)d.ldv * d.Cp);
     } else {
         B = a.Bg;
         V = a.Vg;
+        stage = reinterpret_cast<unsigned char*>(L.svd);
     }
     for (int e = threadIdx.x; e < d.ldb * d.Cp; e += NT) {
         const int r = e % d.ldb, c = e / d.ldb;
@@ -147,32 +156,62 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
                                 default_group_width(d.R, d.C), 0);
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
-    svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg);
-    for (int e = threadIdx.x; e < d.S; e += NT) {
-        const int r = e % d.R, c = e / d.R;
-        float s = 0.f;
-        for (int q = 0; q < nk; ++q) s = fmaf(B[(size_t)L.kept[q] * d.ldb + r], a.Zg[(size_t)q * d.C + c], s);
-        a.A[e] = s;
+    // the solver's SVT: coefficients Z = diag(w / sigma^2) B_K^T M and A = B_K Z, on the tensor
+    // cores for the windows where the solver uses them
+    const bool tc = use_tc_products(d);
+    bool ok = true;
+    if (tc)
+        ok = svt_coeffs_tc(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg, d.Cp, stage, 1, &L.sc->tc);
+    else
+        svt_left_coeffs(a.M, d.R, B, d.ldb, d.R, d.C, L.sigma, L.w, L.kept, nk, a.Zg, d.Cp);
+    float* A = a.A;
+    const int R = d.R;
+    auto put = [=](int r, int c, float v) { A[(size_t)c * R + r] = v; };
+    if (nk > 0 && tc && ok) {
+        const float* Zg = a.Zg;
+        const int* kept = L.kept;
+        const int ldb = d.ldb, ldz = d.Cp;
+        auto la = [=](int r, int q) { return B[(size_t)kept[q] * ldb + r]; };
+        auto lb = [=](int q, int c) { return Zg[(size_t)q * ldz + c]; };
+        ok = tc_gemm<NT, false, false>(d.R, d.C, nk, la, lb, put, stage, TC_KC, 1, &L.sc->tc);
+    } else if (!tc) {
+        for (int e = threadIdx.x; e < d.S; e += NT) {
+            const int r = e % d.R, c = e / d.R;
+            float acc = 0.f;
+            for (int q = 0; q < nk; ++q) acc = fmaf(B[(size_t)L.kept[q] * d.ldb + r], a.Zg[(size_t)q * d.Cp + c], acc);
+            A[e] = acc;
+        }
+    } else if (nk == 0) {
+        for (int e = threadIdx.x; e < d.S; e += NT) A[e] = 0.f;
     }
     for (int k = threadIdx.x; k < d.C; k += NT) a.sigma[k] = L.sigma[k];
-    if (threadIdx.x == 0) a.out->sweeps = sw;
+    if (threadIdx.x == 0) {
+        a.out->sweeps = sw;
+        a.out->status = ok ? 0 : -5;
+    }
+    tc_teardown(&L.sc->tc, TC_TMEM_COLS);
 }
 
 __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     SmemLayout L = carve_smem(smem_raw);
+    tc_setup(&L.sc->tc, TC_TMEM_COLS);
     const Dims d = make_dims(a.m, a.n, a.ttype);
     SvdBufs buf;
     if (a.smem_svd) {
         buf.B = L.svd;
         buf.V = buf.B + (size_t)d.ldb * d.Cp;
         buf.T = buf.V + (size_t)d.ldv * d.Cp;
+        buf.stage = reinterpret_cast<unsigned char*>(buf.T + (size_t)d.ldb * d.Cp);
     } else {
         buf.B = a.Bg;
         buf.V = a.Vg;
         buf.T = a.Tg;
+        buf.stage = reinterpret_cast<unsigned char*>(L.svd);
     }
     buf.Z = a.Zg;
+    buf.nbuf = 1;
+    buf.tc = use_tc_products(d);
     {
         const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
         for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }
@@ -182,6 +221,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     __syncthreads();
     if (!k5_gram(d, a.ttype, a.tau, a.Dhat, a.J, L.sc)) {
         if (threadIdx.x == 0) a.out->status = -2;
+        tc_teardown(&L.sc->tc, TC_TMEM_COLS);
         return;
     }
     double mu0 = a.mu0;
@@ -194,7 +234,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
                              default_group_width(d.R, d.C), nullptr);
     if (threadIdx.x == 0) {
-        a.out->status = io.bad ? -1 : 0;
+        a.out->status = io.tc_timeout ? -5 : io.bad ? -1 : 0;
         a.out->iters = io.iters;
         a.out->sweeps = io.sweeps;
         a.out->c1 = io.c1;
@@ -202,6 +242,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
         a.out->mu = io.mu_last;
         for (int k = 0; k < PMAX; ++k) a.out->dtau[k] = k < a.ttype ? L.sc->cvec[k] : 0.0;
     }
+    tc_teardown(&L.sc->tc, TC_TMEM_COLS);
 }
 
 cudaError_t configure_kernels(size_t max_smem) {

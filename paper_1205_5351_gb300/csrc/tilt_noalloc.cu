@@ -15,7 +15,7 @@ constexpr int NOALLOC_MAX_SIDE = 256;
 constexpr size_t SQ = (size_t)NOALLOC_MAX_SIDE * NOALLOC_MAX_SIDE;   // one 256 x 256 buffer
 constexpr size_t OFF_B = 0;                                          // B: ldb * Cp  (global mode)
 constexpr size_t OFF_V = OFF_B + SQ;                                 // V: ldv * Cp  (global mode)
-constexpr size_t OFF_Z = OFF_V + SQ;                                 // Z: C * C
+constexpr size_t OFF_Z = OFF_V + SQ;                                 // Z: C * Cp
 constexpr size_t OFF_SIG = OFF_Z + SQ;                               // sigma: C
 constexpr size_t OFF_OUT = OFF_SIG + 2 * NOALLOC_MAX_SIDE;           // StepOut record
 constexpr size_t SCRATCH_FLOATS = OFF_OUT + (sizeof(StepOut) + 255) / 4;
@@ -64,7 +64,7 @@ extern "C" int tilt_svt_noalloc(const float* M_dev, int m, int n, float eps, flo
     if (rc) return rc;
     float* s = g_scratch_ptr[dev];
     const Dims d = make_dims(m, n, 0);
-    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes();
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
     SvtArgs a{};
     a.M = M_dev;
     a.A = A_dev;

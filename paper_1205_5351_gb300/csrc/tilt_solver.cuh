@@ -14,7 +14,7 @@ enum { LOOP_GO = 0, LOOP_CONVERGED = 1, LOOP_BAD = 2, LOOP_CANCELLED = 3 };
 
 struct InnerOut {
     int iters, sweeps, warm, rank;
-    bool converged, bad, cancelled;
+    bool converged, bad, cancelled, tc_timeout;
     double c1, c2, mu_last, nuc, l1;
 };
 
@@ -22,7 +22,10 @@ struct SvdBufs {
     float* B;
     float* V;
     float* T;
-    float* Z;   // C x Cp SVT coefficients (shared memory where they fit, else global)
+    float* Z;              // C x Cp SVT coefficients (shared memory where they fit, else global)
+    unsigned char* stage;  // stage buffers of the tensor-core products (shared memory)
+    int nbuf;              // 1 or 2 stage buffers
+    bool tc;               // products on the tensor cores (else register-tiled FP32 SIMT)
 };
 
 __device__ inline unsigned long long clk() { return clock64(); }
@@ -46,7 +49,9 @@ __device__ inline float soft(float x, float eps) {
 //   stop when c1 < eps1 and c2 < eps2; mu <- min(mu_max, rho mu)
 // W^T W v = v - J (G^-1 (J^T v)); the J^T products of A' and E' are accumulated while
 // those planes are produced, so every W^T W costs one extra pass only.
-template <int NCH>
+// TCP: the kernel carries the tensor-core path (the 2-CTA kernel, whose windows are all below
+// the tensor-core size, leaves it out to save registers).
+template <int NCH, bool TCP = true>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
@@ -56,7 +61,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
     InnerOut out;
     out.iters = 0; out.sweeps = 0; out.warm = 0; out.rank = 0;
     out.cancelled = false;
-    out.converged = false; out.bad = false;
+    out.converged = false; out.bad = false; out.tc_timeout = false;
     out.c1 = out.c2 = 0.0; out.mu_last = mu0; out.nuc = 0.0; out.l1 = 0.0;
     unsigned long long t0 = clk();
 
@@ -146,7 +151,14 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         bool warm = haveV && sc->iscal[6];
         if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
         if (warm) {
-            gemm_TV<NCH >= 4 ? 8 : 4>(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
+            if (TCP && buf.tc) {
+                if (!warm_start_tc(buf.T, ldb, buf.V, ldv, buf.B, C, buf.stage, buf.nbuf, &sc->tc)) {
+                    out.bad = out.tc_timeout = true;
+                    break;
+                }
+            } else {
+                gemm_TV<NCH >= 4 ? 8 : 4>(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
+            }
             out.warm++;
         } else {
             for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
@@ -165,40 +177,62 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         const int nk = sc->iscal[1];
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
-        svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp);
+        bool tc_ok = true;
+        if (TCP && buf.tc)
+            tc_ok = svt_coeffs_tc(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp, buf.stage,
+                                  buf.nbuf, &sc->tc);
+        else
+            svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp);
         {
             float acc[1 + PMAX];
 #pragma unroll
             for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
-            // one row of four columns per thread: consecutive threads take consecutive rows (the
-            // B loads and the A, J accesses are coalesced), a float4 of Z (rows at stride Cp,
-            // a broadcast) feeds four FMAs
-            const int nc4 = Cp >> 2;
-            for (int idx = threadIdx.x; idx < R * nc4; idx += NT) {
-                const int c4 = idx / R, r = idx - c4 * R;
-                const int c0 = 4 * c4;
-                float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int q = 0; q < nk; ++q) {
-                    const float b = buf.B[(size_t)L.kept[q] * ldb + r];
-                    const float4 z = *reinterpret_cast<const float4*>(buf.Z + (size_t)q * Cp + c0);
-                    s.x = fmaf(b, z.x, s.x);
-                    s.y = fmaf(b, z.y, s.y);
-                    s.z = fmaf(b, z.z, s.z);
-                    s.w = fmaf(b, z.w, s.w);
-                }
-                const float sv[4] = {s.x, s.y, s.z, s.w};
+            // A' = B_K Z (R x nk times nk x C); the epilogue stores A', accumulates ||A' - A||^2
+            // and J^T A' (consecutive lanes or threads take consecutive rows: the A and J
+            // accesses are coalesced)
+            auto upd = [&](int r, int c, float sa) {
+                const int e = c * R + r;
+                const float da = sa - A[e];
+                acc[0] = fmaf(da, da, acc[0]);
+                A[e] = sa;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (c0 + u >= C) break;
-                    const int e = (c0 + u) * R + r;
-                    const float sa = sv[u];
-                    const float da = sa - A[e];
-                    acc[0] = fmaf(da, da, acc[0]);
-                    A[e] = sa;
+                for (int k2 = 0; k2 < PMAX; ++k2)
+                    if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+            };
+            if (TCP && nk > 0 && buf.tc && tc_ok) {
+                const float* Bb = buf.B;
+                const float* Zb = buf.Z;
+                const int* kept = L.kept;
+                auto la = [=](int r, int q) { return Bb[(size_t)kept[q] * ldb + r]; };
+                auto lb = [=](int q, int c) { return Zb[(size_t)q * Cp + c]; };
+                tc_ok = tc_gemm<NT, false, false>(R, C, nk, la, lb, upd, buf.stage, TC_KC, buf.nbuf, &sc->tc);
+            } else if (nk > 0 && !(TCP && buf.tc)) {
+                // one row of four columns per thread: a float4 of Z (rows at stride Cp, a
+                // broadcast) feeds four FMAs
+                const int nc4 = Cp >> 2;
+                for (int idx = threadIdx.x; idx < R * nc4; idx += NT) {
+                    const int c4 = idx / R, r = idx - c4 * R;
+                    const int c0 = 4 * c4;
+                    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int q = 0; q < nk; ++q) {
+                        const float bq = buf.B[(size_t)L.kept[q] * ldb + r];
+                        const float4 z = *reinterpret_cast<const float4*>(buf.Z + (size_t)q * Cp + c0);
+                        sv.x = fmaf(bq, z.x, sv.x);
+                        sv.y = fmaf(bq, z.y, sv.y);
+                        sv.z = fmaf(bq, z.z, sv.z);
+                        sv.w = fmaf(bq, z.w, sv.w);
+                    }
+                    const float su[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
-                    for (int k2 = 0; k2 < PMAX; ++k2)
-                        if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+                    for (int u = 0; u < 4; ++u)
+                        if (c0 + u < C) upd(r, c0 + u, su[u]);
                 }
+            } else if (nk == 0) {
+                for (int e = threadIdx.x; e < S; e += NT) upd(e % R, e / R, 0.f);
+            }
+            if (!tc_ok) {
+                out.bad = out.tc_timeout = true;
+                break;
             }
             block_sum_f<1 + PMAX>(acc, sc->red);
             if (threadIdx.x == 0) {
@@ -357,7 +391,7 @@ __device__ inline double corner_shift(const double* tau, const double* dtau, int
 }
 
 // Algorithm 1 for one problem.
-template <int NCH>
+template <int NCH, bool TCP = true>
 static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Result& res) {
     Scratch* sc = L.sc;
     const Dims d = make_dims(pr.m, pr.n, pr.p);
@@ -370,7 +404,10 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
         if (pr.smem_svd & 1) { buf.B = sm; sm += nb; } else { buf.B = pr.pl.Bg; }
         if (pr.smem_svd & 2) { buf.V = sm; sm += nv; } else { buf.V = pr.pl.Vg; }
         if (pr.smem_svd & 4) { buf.T = sm; sm += nb; } else { buf.T = pr.pl.Tg; }
-        buf.Z = (pr.smem_svd & 8) ? sm : pr.pl.Zg;      // SVT coefficients (C x C)
+        if (pr.smem_svd & 8) { buf.Z = sm; sm += (size_t)d.C * d.Cp; } else { buf.Z = pr.pl.Zg; }
+        buf.stage = reinterpret_cast<unsigned char*>(sm);  // after the buffers that live in shared memory
+        buf.nbuf = pr.tc_nbuf;
+        buf.tc = pr.tc_nbuf > 0;
     }
     // zero the SVD buffers (padding rows/columns are read by the tiled GEMM)
     {
@@ -423,12 +460,13 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             double mu0 = prm.mu0;
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
             if (threadIdx.x == 0) res.cyc_other += clk() - t1;
-            InnerOut io = k_inner<NCH>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
+            InnerOut io = k_inner<NCH, TCP>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
                                   pr.pl.Mp, buf, haveV, L, &res, pr.jsched, pr.cancel);
             inner_total += io.iters;
             sweeps += io.sweeps;
             warm += io.warm;
             c1 = io.c1; nuc = io.nuc; l1 = io.l1; rank = io.rank;
+            if (io.tc_timeout) { status = -5; break; }
             if (io.bad) { status = -1; break; }
             if (io.cancelled) { status = -4; break; }
             if (!io.converged) inner_maxed = true;

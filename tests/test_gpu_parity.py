@@ -142,8 +142,14 @@ def test_one_inner_iteration_parity(T, ctx, seed, m, n, ttype):
     assert abs(out["c1"] - ref.c1) <= 1e-5 * ref.c1 and abs(out["c2"] - ref.c2) <= 1e-5 * ref.c2
 
 
-@pytest.mark.parametrize("seed,m,n,ttype", [(51, 50, 50, 6), (52, 64, 45, 8), (53, 120, 110, 6)])
+@pytest.mark.parametrize("seed,m,n,ttype", [(51, 50, 50, 6), (52, 64, 45, 8), (53, 120, 110, 6),
+                                            (54, 200, 170, 8)])
 def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
+    # The 200 x 170 window runs its dense products (warm start, SVT coefficients and
+    # reconstruction) on the tensor cores in 3xTF32, whose error per product (~1e-6 relative,
+    # the probe of the product engine measured 5e-7 to 1.4e-6) is about ten times that of the
+    # FP32 SIMT products of the smaller windows; carried through the loop it left E at 1.7e-4
+    # relative (measured), so E is held to 1e-3 there, everything else as below.
     # the whole inner loop to convergence: the FP32 rounding of every iteration (about
     # 1e-7 relative, see the one-iteration test) carries into the next over 56-73
     # iterations, so the converged A, E and dtau are compared at 1e-4 relative (measured:
@@ -160,8 +166,9 @@ def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
     assert ref.converged
     A = T.from_long_layout(A_d.cpu().numpy(), m, n)
     E = T.from_long_layout(E_d.cpu().numpy(), m, n)
+    tc_window = min(m, n) >= 160
     assert rel(A, ref.A) <= 1e-4, rel(A, ref.A)
-    assert rel(E, ref.E) <= 1e-4, rel(E, ref.E)
+    assert rel(E, ref.E) <= (1e-3 if tc_window else 1e-4), rel(E, ref.E)
     dt_ref = O.delta_tau(O.WtW(J, Q), ref.A, ref.E, Dh)
     assert rel(out["dtau"], dt_ref) <= 1e-4, rel(out["dtau"], dt_ref)
     assert abs(out["iters"] - ref.iters) <= 1, (out["iters"], ref.iters)
