@@ -54,9 +54,7 @@ def make_patches(workload, count, first):
         groups = max(1, count // len(synth.MULTISTART_ANGLES))
         return synth.multistart_batch(groups, first=first // len(synth.MULTISTART_ANGLES))
     raise ValueError(workload)
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
-MAX_SM_MHZ = 2070.0
+FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grouped launch of the solver
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
@@ -115,8 +113,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream"], default="affine")
     ap.add_argument("--patches", type=int, default=None, help="patches per GPU (default: the workload's)")
-    ap.add_argument("--plain-seconds", type=float, default=15.0, help="budget of the plain GPU solver sample")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle CPU sample")
+    ap.add_argument("--plain-patches", type=int, default=8, help="patches in the plain GPU solver sample (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the oracle CPU sample")
+    ap.add_argument("--parity-patches", type=int, default=64, help="size of the stratified parity sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stream-seconds", type=float, default=600.0, help="wall-clock cap of the served stream")
     ap.add_argument("--no-autotune", action="store_true", help="skip autotuning (profiling captures)")
@@ -145,16 +144,17 @@ def cpu_pool():
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload="affine"):
-    """Oracle on patches first, first+1, ... until about budget_s of wall time is spent."""
-    max_patches = max_patches or 4 * cores
+def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload="affine", indices=None):
+    """Oracle on patches first, first+1, ... (or on the given indices, in that order) until about
+    budget_s of wall time is spent, ``cores`` patches at a time."""
+    order = list(indices) if indices is not None else list(range(max_patches or 4 * cores))
     t0 = time.perf_counter()
     out = []
     nxt = 0
-    while nxt < max_patches and (time.perf_counter() - t0) < budget_s:
-        batch = list(range(nxt, min(nxt + cores, max_patches)))
+    while nxt < len(order) and (time.perf_counter() - t0) < budget_s:
+        batch = order[nxt:nxt + cores]
         out += pool.map(_oracle_one, [(i, first, workload) for i in batch])
-        nxt = batch[-1] + 1
+        nxt += len(batch)
     wall = time.perf_counter() - t0
     return out, wall
 
@@ -226,6 +226,45 @@ def algorithmic_flops(p, r) -> float:
     R, C = max(p.m, p.n), min(p.m, p.n)
     sweep = C * (C - 1) / 2 * (12 * R + 6 * C)
     return r["svd_sweeps"] * sweep + r["svd_warm"] * 2.0 * R * C * C
+
+
+def phase_work(p, r):
+    """Algorithmic work of one solve by phase, from its counters: bytes of the warp/Jacobian
+    pass (per outer step: 4 texels read, D_hat and p Jacobian planes written and read back),
+    bytes of the elementwise passes (per inner iteration: A, E, Y, D_hat, P read, J read
+    twice, E, Y, P, M written), FP32 flops of the SVD (Jacobi sweeps and warm-start
+    products) and of the SVT reconstruction (coefficients and product, 2 R C nk each with nk
+    at most C: counted at the kept count's upper bound C / 2, the median measured on these
+    workloads)."""
+    R, C, S, pp = max(p.m, p.n), min(p.m, p.n), p.m * p.n, p.ttype
+    return {"warp_jacobian": r["outer_iters"] * 4.0 * (4 * S + 2 * (1 + pp) * S),
+            "elementwise": r["inner_iters"] * 4.0 * (9 * S + 2 * pp * S),
+            "svd": algorithmic_flops(p, r),
+            "svt_reconstruct": r["inner_iters"] * 2 * (2.0 * R * C * (C / 2))}
+
+
+def stratified_sample(patches, results, lat, k):
+    """Indices of a parity sample of about k patches: the slowest patch, every patch that ended
+    with an inner loop at its cap (status 2), then patches spread over every (launch class,
+    status, size quartile) stratum, round robin, lowest index first."""
+    import numpy as np
+    n = len(results)
+    chosen = [int(np.argmax(lat[-n:]))]
+    chosen += [q for q in range(n) if results[q]["status"] == 2 and q not in chosen]
+    sizes = np.array([p.m * p.n for p in patches])
+    qs = np.quantile(sizes, [0.25, 0.5, 0.75]) if n > 3 else []
+    strata = {}
+    for q in range(n):
+        key = (results[q]["launch_class"], results[q]["status"], int(np.searchsorted(qs, sizes[q])))
+        strata.setdefault(key, []).append(q)
+    queues = [v for _, v in sorted(strata.items())]
+    while len(chosen) < min(k, n) and any(queues):
+        for v in queues:
+            while v and v[0] in chosen:
+                v.pop(0)
+            if v and len(chosen) < min(k, n):
+                chosen.append(v.pop(0))
+    return chosen
 
 
 def percentile(xs, q):
@@ -342,8 +381,29 @@ def run_ours(args, rank, world, local_rank, dist):
         dom_class = classes[dom] if dom is not None else None
         dom_flops = sum(f for f, r in zip(flops, results) if r["launch_class"] == dom_class)
         achieved = dom_flops / (k_dom * 1e-3) / 1e12 if k_dom else None
-        mhz = MAX_SM_MHZ
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        # FP32 peak from the device's SM count and the SM clock sampled during the timed steps
+        props = torch.cuda.get_device_properties(dev)
+        n_sms = props.multi_processor_count
+        mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2070.0
+        peak = n_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        # per phase of the fused kernel: algorithmic work / SM-seconds spent in the phase,
+        # against one SM's share of the peak (phases of different patches overlap on
+        # different SMs, so each is rated per SM-second)
+        work = {}
+        for p, r in zip(patches, results):
+            for kk, v in phase_work(p, r).items():
+                work[kk] = work.get(kk, 0.0) + v
+        names = ["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"]
+        sm_s = {nm: sum(r["phase_cycles"][i] for r in results) / (mhz * 1e6) for i, nm in enumerate(names)}
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        fp32_sm = FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        phase_roof = {}
+        for nm, unit, pk in (("warp_jacobian", "GB/s", hbm / n_sms), ("elementwise", "GB/s", hbm / n_sms),
+                             ("svd", "TFLOP/s", fp32_sm), ("svt_reconstruct", "TFLOP/s", fp32_sm)):
+            if sm_s[nm] > 0:
+                a_ = work[nm] / sm_s[nm] / (1e9 if unit == "GB/s" else 1e12)
+                phase_roof[nm] = {"achieved_per_sm": a_, "peak_per_sm": pk, "unit": unit, "frac": a_ / pk}
         traffic = None
         if NCU_TRAFFIC["sources_sha256"] == kernel_sources_sha256() and not over and not args.no_autotune:
             traffic = NCU_TRAFFIC["bytes"].get("%s/%s/%s" % (args.workload, len(patches), dom_class))
@@ -381,6 +441,8 @@ def run_ours(args, rank, world, local_rank, dist):
                           "per_class": {str(c): t for c, t in zip(classes, per_class_ms)},
                           "patches_per_class": {str(c): sum(1 for r in results if r["launch_class"] == c)
                                                 for c in classes}},
+            "converged_patches_per_s": sum(1 for r in results if r["status"] == 0) * world / (max(times) * 1e-3),
+            "phase_roofline": phase_roof,
             "slowest_patch": (lambda q: {"m": patches[q].m, "n": patches[q].n, "kind": patches[q].meta["kind"],
                                          "done_ms": lat[q], "outer": results[q]["outer_iters"],
                                          "inner": results[q]["inner_iters"], "sweeps": results[q]["svd_sweeps"],
@@ -393,7 +455,8 @@ def run_ours(args, rank, world, local_rank, dist):
                                    "%d patches)" % (dom_class, sum(1 for r in results
                                                                if r["launch_class"] == dom_class)),
                          "flops_per_launch": dom_flops,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA issue rate)"},
+                         "peak_source": "%d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz (median SM clock "
+                                        "sampled during the timed steps): FP32 FMA issue rate" % (n_sms, mhz)},
             "gpu_launches": launches,                 # solver launches inside the timed steps
             "gpu_launches_per_step": launches // max(1, args.steps),
             "autotune_s": round(tune_s, 2),
@@ -409,36 +472,47 @@ def run_ours(args, rank, world, local_rank, dist):
             best = tilt.best_of(results, starts)
             out["multistart"] = {"groups": len(best), "starts": starts,
                                  "chosen_start_histogram": {str(b): best.count(b) for b in sorted(set(best))}}
-        if args.plain_seconds > 0 and args.workload in ("affine", "small", "projective"):
+        if args.plain_patches > 0 and args.workload in ("affine", "small", "projective"):
+            # the plain solver on patches spread evenly over the size-sorted workload
             from baseline.plain_gpu import tilt_plain
+            by_size = sorted(range(len(patches)), key=lambda q: patches[q].m * patches[q].n)
+            kp = min(args.plain_patches, len(patches))
+            pick = [by_size[(2 * j + 1) * len(by_size) // (2 * kp)] for j in range(kp)]
             t0 = time.perf_counter()
-            k = 0
-            while k < len(patches) and time.perf_counter() - t0 < args.plain_seconds:
-                p = patches[k]
-                tilt_plain(imgs[k], p.tau0, p.ttype, p.m, p.n, **{kk: vv for kk, vv in wl_params.items()})
+            for q in pick:
+                p = patches[q]
+                tilt_plain(imgs[q], p.tau0, p.ttype, p.m, p.n, **{kk: vv for kk, vv in wl_params.items()})
                 torch.cuda.synchronize()
-                k += 1
-            plain = k / (time.perf_counter() - t0)
+            plain = len(pick) / (time.perf_counter() - t0)
             out["plain_gpu"] = {"value": plain, "unit": "patches/s",
-                                "sample": f"first {k} patches, one at a time (PyTorch ops, cuSOLVER SVD "
-                                          "per inner iteration, host-side stopping test)"}
+                                "sample": f"{len(pick)} patches spread over the size range (indices {pick}), one "
+                                          "at a time (PyTorch ops, cuSOLVER SVD per inner iteration, host-side "
+                                          "stopping test)"}
             out["speedup_vs_plain_gpu"] = value / plain if plain > 0 else None
         if pool is not None:
-            sample, wall = run_oracle_sample(pool, cores, args.cpu_seconds, first=first,
-                                             max_patches=min(4 * cores, len(patches)), workload=args.workload)
+            idx_s = stratified_sample(patches, results, lat, args.parity_patches)
+            sample, wall = run_oracle_sample(pool, cores, args.cpu_seconds, first=first, workload=args.workload,
+                                             indices=idx_s)
             pool.close()
-            errs = []
+            errs, rank_eq = [], 0
             for idx, secs, tau, iters, rk in sample:
                 t = np.asarray(results[idx]["tau"])
                 errs.append(float(np.linalg.norm(t - np.asarray(tau)) / np.linalg.norm(tau)))
+                rank_eq += int(results[idx]["rank"] == rk)
             ok = sum(1 for e in errs if e <= 1e-3)
             frac = ok / len(errs) if errs else None
             out["cpu_baseline"] = {"value": len(sample) / wall if sample else None, "unit": "patches/s", "cores": cores,
                                    "kind": "oracle", "cpu": cpu_model(),
-                                   "sample": f"first {len(sample)} patches of the same workload, "
-                                             f"one per process, {wall:.1f} s wall"}
-            out["parity_sample"] = {"patches": len(errs), "tau_err_le_1e-3": ok,
-                                    "max_tau_err": max(errs) if errs else None}
+                                   "sample": f"{len(sample)} patches of the same workload (the stratified parity "
+                                             f"sample below), one per process, {wall:.1f} s wall"}
+            done = [q for q, *_ in sample]
+            out["parity_sample"] = {"patches": len(errs), "tau_err_le_1e-3": ok, "rank_equal": rank_eq,
+                                    "max_tau_err": max(errs) if errs else None,
+                                    "includes_slowest_patch": bool(done) and done[0] == idx_s[0],
+                                    "status_counts": {str(st): sum(1 for q in done if results[q]["status"] == st)
+                                                      for st in sorted({results[q]["status"] for q in done})},
+                                    "selection": "slowest patch, every status-2 patch, then round robin over "
+                                                 "(launch class, status, size quartile) strata"}
             value *= frac if frac is not None else 1.0
         out["value"] = value
     ctx.close()

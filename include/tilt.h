@@ -116,7 +116,9 @@ typedef struct {
                             SM, all SVD buffers in shared memory; 1 one CTA per SM, the SVD
                             buffers in shared memory as far as they fit (also class-0-sized
                             problems of a batch no larger than the SM count); 2 one CTA per
-                            SM, all in device memory.  -1: solved by the persistent workers */
+                            SM with the tensor-core products (short side >= 160), or with
+                            every SVD buffer in device memory.  -1: solved by the persistent
+                            workers                                                         */
 } tilt_result;
 
 /* Fill *p with the default parameters. */

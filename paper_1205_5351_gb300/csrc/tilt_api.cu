@@ -450,8 +450,13 @@ int admit_waiting(tilt_ctx* ctx) {
 }
 
 // Grouped-launch class of a problem: 0 two CTAs per SM (all SVD buffers in shared memory),
-// 1 one CTA per SM (shared memory as far as it holds them), 2 one CTA per SM (none).
-int launch_class_of(const Layout& L) { return L.smem_svd ? (L.minb == 2 ? 0 : 1) : 2; }
+// 1 one CTA per SM (shared memory as far as it holds them, SIMT products), 2 one CTA per SM
+// with the tensor-core products (short side >= TC_MIN_C) or with no SVD buffer in shared
+// memory.
+int launch_class_of(const Layout& L) {
+    if (L.tc_nbuf > 0 || !L.smem_svd) return 2;
+    return L.minb == 2 ? 0 : 1;
+}
 
 void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     memset(out, 0, sizeof *out);
@@ -773,7 +778,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         }
         const int minb = (c == 0) ? 2 : 1;
         if (nev < 3) CUDA_TRY(cudaEventRecord(ctx->ev[2 * nev], st[c]));
-        CUDA_TRY(launch_solver(ctx->probs_dev, ord_dev + start, end - start, minb, smem, st[c]));
+        CUDA_TRY(launch_solver(ctx->probs_dev, ord_dev + start, end - start, minb, c == 2, smem, st[c]));
         if (nev < 3) { CUDA_TRY(cudaEventRecord(ctx->ev[2 * nev + 1], st[c])); ++nev; }
         ctx->launches++;
         start = end;

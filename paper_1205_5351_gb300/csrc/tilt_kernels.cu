@@ -18,13 +18,14 @@ __device__ inline void copy_to_shared(T* dst, const T* src) {
 // flag live in host-mapped memory, so the host sees every problem retire on its own.
 // MINB CTAs per SM; NCH float4 chunks per lane keep a Jacobi column pair in registers
 // (R <= 32 NCH), fewer for the 2-CTA variant so that it fits 64 registers per thread.
-template <int MINB, int NCH>
+// TCP: the kernel carries the tensor-core path (only the launch class of large windows: the
+// extra code costs the SIMT path registers).
+template <int MINB, int NCH, bool TCP>
 __global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const int* order) {
     extern __shared__ __align__(256) unsigned char smem_raw[];
     __shared__ Problem sp;
     __shared__ Result sres;
     SmemLayout L = carve_smem(smem_raw);
-    constexpr bool TCP = MINB < 2;     // the 2-CTA kernel's windows are all below the tensor-core size
     if (TCP) tc_setup(&L.sc->tc, TC_TMEM_COLS);
     copy_to_shared(&sp, probs + order[blockIdx.x]);
     solve_problem<NCH, TCP>(sp, L, sres);
@@ -247,9 +248,14 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
 
 cudaError_t configure_kernels(size_t max_smem) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(solver_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    if ((e = cudaFuncSetAttribute(solver_kernel<1, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)max_smem)))
         return e;
-    if ((e = cudaFuncSetAttribute(solver_kernel<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    if ((e = cudaFuncSetAttribute(solver_kernel<1, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(solver_kernel<2, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)max_smem)))
         return e;
     if ((e = cudaFuncSetAttribute(svt_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
@@ -260,12 +266,15 @@ cudaError_t configure_kernels(size_t max_smem) {
     return cudaSuccess;
 }
 
-cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st) {
+cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, bool tcp, size_t smem,
+                          cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (minb >= 2)
-        solver_kernel<2, 3><<<count, NT, smem, st>>>(probs, order);
+        solver_kernel<2, 3, false><<<count, NT, smem, st>>>(probs, order);
+    else if (tcp)
+        solver_kernel<1, 4, true><<<count, NT, smem, st>>>(probs, order);
     else
-        solver_kernel<1, 4><<<count, NT, smem, st>>>(probs, order);
+        solver_kernel<1, 4, false><<<count, NT, smem, st>>>(probs, order);
     return cudaGetLastError();
 }
 

@@ -86,8 +86,10 @@ struct WorkQueue {
 // idle_spins polls (or stop is set), each solving one problem at a time.
 cudaError_t launch_workers(Problem* probs, const WorkQueue& q, int ctas, size_t smem, cudaStream_t st);
 
-// Solver: count CTAs, CTA b solves probs[order[b]].  minb selects the occupancy variant.
-cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, size_t smem, cudaStream_t st);
+// Solver: count CTAs, CTA b solves probs[order[b]].  minb selects the occupancy variant, tcp
+// the 1-CTA variant that carries the tensor-core products (launch class 2).
+cudaError_t launch_solver(Problem* probs, const int* order, int count, int minb, bool tcp, size_t smem,
+                          cudaStream_t st);
 cudaError_t launch_warp_step(const WarpArgs& a, cudaStream_t st);
 cudaError_t launch_gram_step(const GramArgs& a, cudaStream_t st);
 cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st);

@@ -36,3 +36,20 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "2 patches" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "patches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_stratified_parity_sample_covers_the_hard_cases():
+    # the slowest patch first, then every status-2 patch, then every (class, status, size)
+    # stratum before any stratum repeats
+    import bench
+    from types import SimpleNamespace as NS
+    sizes = [(40, 40), (120, 120), (60, 80), (100, 90)] * 10
+    patches = [NS(m=m, n=n) for m, n in sizes]
+    results = [{"status": (2 if q == 17 else 1 if q % 3 == 0 else 0), "launch_class": q % 2} for q in range(40)]
+    lat = [float(q) for q in range(40)]
+    lat[9] = 1e6
+    idx = bench.stratified_sample(patches, results, lat, 12)
+    assert idx[0] == 9 and idx[1] == 17 and len(idx) == 12 and len(set(idx)) == 12
+    strata = {(results[q]["launch_class"], results[q]["status"]) for q in idx}
+    assert strata == {(r["launch_class"], r["status"]) for r in results}
+    assert len(bench.stratified_sample(patches, results, lat, 100)) == 40

@@ -149,7 +149,8 @@ def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
     # reconstruction) on the tensor cores in 3xTF32, whose error per product (~1e-6 relative,
     # the probe of the product engine measured 5e-7 to 1.4e-6) is about ten times that of the
     # FP32 SIMT products of the smaller windows; carried through the loop it left E at 1.7e-4
-    # relative (measured), so E is held to 1e-3 there, everything else as below.
+    # and dtau at 1.1e-4 relative (measured), so those two are held to 1e-3 there, everything
+    # else as below.
     # the whole inner loop to convergence: the FP32 rounding of every iteration (about
     # 1e-7 relative, see the one-iteration test) carries into the next over 56-73
     # iterations, so the converged A, E and dtau are compared at 1e-4 relative (measured:
@@ -170,7 +171,7 @@ def test_inner_loop_parity(T, ctx, seed, m, n, ttype):
     assert rel(A, ref.A) <= 1e-4, rel(A, ref.A)
     assert rel(E, ref.E) <= (1e-3 if tc_window else 1e-4), rel(E, ref.E)
     dt_ref = O.delta_tau(O.WtW(J, Q), ref.A, ref.E, Dh)
-    assert rel(out["dtau"], dt_ref) <= 1e-4, rel(out["dtau"], dt_ref)
+    assert rel(out["dtau"], dt_ref) <= (1e-3 if tc_window else 1e-4), rel(out["dtau"], dt_ref)
     assert abs(out["iters"] - ref.iters) <= 1, (out["iters"], ref.iters)
     assert O.numerical_rank(A) == O.numerical_rank(ref.A)
 
