@@ -17,6 +17,8 @@ What it computes (paper section / equation named on every function):
   the SVD warm start of Algorithm 2 (Sec. 5, Appendix A).
 * Steps 3-4 of Algorithm 1: dtau (Eq. Delta_tau, stacked with Q as in
   Eq. two_linear_constraint) and tau <- tau + dtau.
+* The comparison method of Sec. 2.2: the ADM of Zhang et al. for the inner loop
+  (Eq. TILT_3), with the three blocks A, E, dtau updated in turn and mu <- rho mu.
 
 Readings of points where the paper is silent or inconsistent (each is listed in the
 design notes of the repository):
@@ -45,6 +47,9 @@ design notes of the repository):
       outer_tol pixels, or after max_outer steps.
 * R9  A_0 is the normalised D o tau^0.
 * R10 The SVD runs on the m x n matrix as given; singular values are non-negative.
+* R16 ADM (Sec. 2.2) parameters, not printed: mu_0 = 1.25/||D||_2, rho = 1.25, stop when
+      ||D + J dtau - A - E||_F / ||D||_F < 1e-7 (the usual inexact-ALM settings of the cited
+      line of work).
 """
 from __future__ import annotations
 
@@ -374,6 +379,69 @@ def delta_tau(op: WtW, A, E, Dhat) -> np.ndarray:
     solution of the stacked system of Eq. two_linear_constraint (Eq. Delta_tau when Q is
     absent)."""
     return op.coeffs(A + E - Dhat)
+
+
+# ============================================================================ ADM baseline (Sec. 2.2)
+@dataclasses.dataclass
+class AdmParams:
+    """Parameters of the ADM of Zhang et al. for the inner loop (values the paper leaves open
+    are readings: R16)."""
+
+    lam: float = -1.0            # <= 0 -> 1/sqrt(max(m, n))
+    tol: float = 1e-7            # stop when ||D + J dtau - A - E||_F / ||D||_F < tol
+    rho: float = 1.25            # mu <- rho mu
+    mu0: float = -1.0            # <= 0 -> 1.25/||D||_2
+    max_iter: int = 1000
+
+
+@dataclasses.dataclass
+class AdmResult:
+    A: np.ndarray
+    E: np.ndarray
+    Y: np.ndarray
+    dtau: np.ndarray
+    iters: int
+    converged: bool
+    residual: float
+
+
+def adm_inner(D, J, lam, prm: AdmParams) -> AdmResult:
+    """The ADM of Zhang et al. as Sec. 2.2 states it: minimise the augmented Lagrangian of
+    Eq. TILT_3, L = ||A||_* + lam||E||_1 + <Y, D + J dtau - A - E> + mu/2 ||D + J dtau - A - E||^2,
+    over A, E and dtau in turn (Gauss-Seidel), then update Y and mu:
+        A_k+1    = S_{1/mu}(D + J dtau_k - E_k + Y_k/mu)        (minimiser over A, Eq. A_1)
+        E_k+1    = T_{lam/mu}(D + J dtau_k - A_k+1 + Y_k/mu)    (minimiser over E, Eq. E_1)
+        dtau_k+1 = (J^T J)^{-1} J^T (A_k+1 + E_k+1 - D - Y_k/mu)  (least squares in dtau)
+        Y_k+1    = Y_k + mu (D + J dtau_k+1 - A_k+1 - E_k+1),   mu_k+1 = rho mu_k
+    from A_0 = D, E_0 = 0, dtau_0 = 0, Y_0 = 0 (Sec. 6.1).  D is an m x n array, J is
+    (m n) x p with rows in row-major pixel order."""
+    D = np.asarray(D, dtype=np.float64)
+    J = np.asarray(J, dtype=np.float64)
+    shape = D.shape
+    d = D.reshape(-1)
+    G = J.T @ J
+    mu = 1.25 / float(np.linalg.norm(D, 2)) if prm.mu0 <= 0 else float(prm.mu0)
+    A = D.copy()
+    E = np.zeros(shape)
+    Y = np.zeros(shape)
+    dtau = np.zeros(J.shape[1])
+    nD = float(np.linalg.norm(D))
+    res = math.inf
+    converged = False
+    k = 0
+    for k in range(1, prm.max_iter + 1):
+        Jd = (J @ dtau).reshape(shape)
+        A = svt(D + Jd - E + Y / mu, 1.0 / mu)[0]
+        E = soft_threshold(D + Jd - A + Y / mu, lam / mu)
+        dtau = np.linalg.solve(G, J.T @ (A + E - D - Y / mu).reshape(-1)) if J.shape[1] else dtau
+        R = D + (J @ dtau).reshape(shape) - A - E
+        Y = Y + mu * R
+        res = float(np.linalg.norm(R)) / nD
+        if res < prm.tol:
+            converged = True
+            break
+        mu = prm.rho * mu
+    return AdmResult(A, E, Y, dtau, k, converged, res)
 
 
 # ============================================================================ Algorithm 1

@@ -492,3 +492,70 @@ def test_svdws_accuracy_bound():
             assert lhs <= np.linalg.norm(Mprev - M) + 1e-12
         # the step decreases f
         assert O.curve_objective(M, *ws) <= O.curve_objective(M, U, s, Vt.T)
+
+
+# ------------------------------------------------------------------ ADM baseline (Sec. 2.2)
+@pytest.mark.parametrize("size", [10, 50, 100])
+def test_adm_reproduces_table_numerical(size):
+    # Table 1's ADM column: objective and iteration count at which the ADM of Zhang et al.
+    # stops on the inner-loop-only data (R14 distribution, R16 parameters), 10 trials
+    rows = json.load(open(os.path.join(GOLDEN, "table_numerical.json")))["rows"]
+    row = {r[0]: r for r in rows}[size]
+    want_obj, want_it = row[1], row[5]
+    objs, its = [], []
+    for trial in range(10):
+        rng = np.random.default_rng(1000 + trial)
+        D, J = synth.random_inner_problem(rng, size, size, 6)
+        D = D - 0.5
+        lam = 1 / math.sqrt(size)
+        r = O.adm_inner(D, J, lam, O.AdmParams())
+        assert r.converged
+        objs.append(O.objective(r.A, r.E, lam))
+        its.append(r.iters)
+    assert abs(np.mean(objs) - want_obj) / want_obj < 0.02
+    assert abs(np.mean(its) - want_it) / want_it < 0.1
+
+
+def test_adm_rpca_special_case_exact_recovery():
+    # with no Jacobian the ADM is the inexact augmented Lagrangian method of RPCA: a rank-3 +
+    # 5 %-sparse 50 x 50 matrix is recovered with lambda = 1/sqrt(50)
+    rng = np.random.default_rng(9)
+    m = n = 50
+    L = rng.standard_normal((m, 3)) @ rng.standard_normal((3, n)) / math.sqrt(n)
+    S = np.zeros((m, n))
+    mask = rng.random((m, n)) < 0.05
+    S[mask] = rng.uniform(-1, 1, mask.sum())
+    res = O.adm_inner(L + S, np.zeros((m * n, 0)), 1 / math.sqrt(50), O.AdmParams(tol=1e-9, rho=1.1))
+    assert res.converged
+    assert np.linalg.norm(res.A - L) / np.linalg.norm(L) < 1e-5
+    assert np.linalg.norm(res.E - S) / np.linalg.norm(S) < 1e-5
+
+
+def test_adm_kkt_at_convergence():
+    # optimality of the stopping point of Eq. TILT_3 with L's +<Y, .> sign: Y in d||A||_*,
+    # Y in lam d||E||_1, J^T Y = 0 (stationarity in dtau), D + J dtau = A + E.  The three-block
+    # ADM carries no convergence guarantee (Sec. 2.2), so the dual conditions are checked at a
+    # slow penalty growth (rho = 1.05), where they hold to 1e-3; and its objective is that of
+    # the LADMAP optimum on the same data
+    rng = np.random.default_rng(3)
+    m, n, p = 40, 36, 6
+    D, J = synth.random_inner_problem(rng, m, n, p)
+    D = D - 0.5
+    lam = 1 / math.sqrt(max(m, n))
+    r = O.adm_inner(D, J, lam, O.AdmParams(tol=1e-10, rho=1.05, max_iter=5000))
+    assert r.converged
+    Y = r.Y
+    tol = 1e-3
+    U, s, Vt = np.linalg.svd(r.A, full_matrices=False)
+    k = int(np.sum(s > 1e-6 * s[0]))
+    assert np.linalg.norm(Y, 2) <= 1 + tol
+    np.testing.assert_allclose(U[:, :k].T @ Y @ Vt[:k].T, np.eye(k), atol=tol)
+    supp = np.abs(r.E) > 1e-9
+    assert supp.sum() > 0
+    np.testing.assert_allclose(Y[supp], lam * np.sign(r.E[supp]), atol=tol * lam)
+    assert np.abs(Y[~supp]).max() <= lam * (1 + tol)
+    assert np.abs(J.T @ Y.reshape(-1)).max() <= 1e-8 * np.abs(Y).max()
+    assert np.linalg.norm(D + (J @ r.dtau).reshape(m, n) - r.A - r.E) <= 1e-10 * np.linalg.norm(D)
+    ref = O.inner_ladmap(D, J, None, lam, D, 0 * D, 0 * D, O.Params(eps1=1e-10, eps2=1e-4, max_inner=20000))
+    assert ref.converged
+    assert abs(O.objective(r.A, r.E, lam) - O.objective(ref.A, ref.E, lam)) <= 1e-5 * O.objective(ref.A, ref.E, lam)
