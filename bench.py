@@ -39,6 +39,11 @@ WORKLOADS = {
                    "+-25 deg, skew +-0.2, perspective +-1e-3, 10 % corruption", 256, {}),
     "multistart": ("64 projective 512x512 patches, rank-5 texture, 10 % corruption, 9 starts each "
                    "(initial rotations -40..40 deg), lowest objective kept", 576, {}),
+    "convergence": ("range of convergence (Sec. 6.2): 231 checkerboards 60x60 (period 12) deformed by "
+                    "R(theta)[[1, t], [0, 1]], theta 0..30 deg step 3, skew 0..1 step 0.05, rectified from "
+                    "the identity, at most 40 outer steps", 231, {"max_outer": 40}),
+    "corruption": ("robustness (Sec. 6.2): 10 rank-3 textures 60x60 rotated 10 deg, 0..100 % of the pixels "
+                   "replaced by Uniform[0, 1] in steps of 5 %, at most 40 outer steps", 210, {"max_outer": 40}),
 }
 
 
@@ -53,6 +58,10 @@ def make_patches(workload, count, first):
     if workload == "multistart":
         groups = max(1, count // len(synth.MULTISTART_ANGLES))
         return synth.multistart_batch(groups, first=first // len(synth.MULTISTART_ANGLES))
+    if workload == "convergence":
+        return synth.convergence_grid(count, first=first)
+    if workload == "corruption":
+        return synth.corruption_sweep(count, first=first)
     raise ValueError(workload)
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
 
@@ -467,6 +476,10 @@ def run_ours(args, rank, world, local_rank, dist):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
         value = n_total / (float(tot[0]) * 1e-3)
+        if args.workload in ("convergence", "corruption"):
+            from paper_1205_5351_gb300 import sweeps
+            out["sweep"] = (sweeps.convergence_map if args.workload == "convergence"
+                            else sweeps.corruption_rates)(patches, results)
         if args.workload == "multistart":
             starts = len(synth.MULTISTART_ANGLES)
             best = tilt.best_of(results, starts)

@@ -236,7 +236,8 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
              float* sigma_out, int* sweeps_out);
 
 /* The inner loop of Algorithm 1 (Eqs. A, E, Y, mu, rho, Cond1, Cond2 in the W^T W form of
- * Eq. newvars2) on given D_hat, J and tau (tau gives Q).  A_dev, E_dev, Y_dev are the warm
+ * Eq. newvars2) on given D_hat, J and tau (tau gives Q; tau = NULL: no constraint rows, so
+ * W^T W = J_perp of Sec. 4.1, as in the inner-loop-only experiment of Sec. 6.1).  A_dev, E_dev, Y_dev are the warm
  * start on entry (Y is projected by W^T W first, Eq. Y_new_warmstart) and the result on
  * exit.  mu0 <= 0 -> 1.25 / ||D_hat||_2.  Outputs (host, may be NULL): *iters_out,
  * dtau_out[p] (Eq. Delta_tau with Q), *c1_out, *c2_out, *mu_out (last mu used). */
@@ -244,6 +245,25 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
                const double* tau, tilt_transform type, const tilt_params* params, double mu0,
                float* A_dev, float* E_dev, float* Y_dev, int* iters_out, double* dtau_out,
                double* c1_out, double* c2_out, double* mu_out);
+
+/* The comparison method of Sec. 2.2: the alternating direction method (ADM) of Zhang et al.
+ * for the inner loop, Eq. TILT_3 (min ||A||_* + lambda ||E||_1 s.t. D + J dtau = A + E), on
+ * given D and J with no constraint rows.  It minimises the augmented Lagrangian over A, E and
+ * dtau in turn (A' = S_{1/mu}(D + J dtau - E + Y/mu), E' = T_{lambda/mu}(D + J dtau - A' + Y/mu),
+ * dtau' = (J^T J)^-1 J^T (A' + E' - D - Y/mu)), then Y' = Y + mu (D + J dtau' - A' - E') and
+ * mu <- rho mu, from A = D, E = 0, dtau = 0, Y = 0, until ||D + J dtau - A - E||_F / ||D||_F <
+ * tol.  The SVT is the solver's (one-sided Jacobi, warm-started from the previous V).
+ * D_dev: m x n device plane (layout above); J_dev: p such planes, 0 <= p <= 8 (NULL when
+ * p = 0).  params (may be NULL): lambda (<= 0 -> 1/sqrt(max(m, n))), eps1 = tol (default
+ * 1e-5; Sec. 6.1's comparison uses 1e-7), rho0 = rho > 1 (default 1.5; 1.25 reproduces
+ * Table 1's ADM column), max_inner = iteration cap; the other fields are ignored.
+ * mu0 <= 0 -> 1.25 / ||D||_2.  A_dev, E_dev, Y_dev (device, m x n) receive the result.
+ * Outputs (host, may be NULL): *iters_out, dtau_out[p], *residual_out (the last relative
+ * constraint residual; >= tol when the cap was reached), *sweeps_out (Jacobi sweeps).
+ * Errors: TILT_E_INVAL (also for a singular J^T J), TILT_E_TIMEOUT, TILT_E_CUDA. */
+int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m, int n, int p,
+                   const tilt_params* params, double mu0, float* A_dev, float* E_dev, float* Y_dev,
+                   int* iters_out, double* dtau_out, double* residual_out, int* sweeps_out);
 
 /* ------------------------------------------------------------------------------------------
  * Allocation-free singular value thresholding.  (The paper has no counterpart: this is a

@@ -1089,7 +1089,7 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
 int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, int n, const double* tau, tilt_transform type,
                const tilt_params* params, double mu0, float* A_dev, float* E_dev, float* Y_dev, int* iters_out,
                double* dtau_out, double* c1_out, double* c2_out, double* mu_out) {
-    if (!ctx || !Dhat_dev || !J_dev || !tau || !A_dev || !E_dev || !Y_dev) return fail(TILT_E_INVAL, "null argument");
+    if (!ctx || !Dhat_dev || !J_dev || !A_dev || !E_dev || !Y_dev) return fail(TILT_E_INVAL, "null argument");
     if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "window %d x %d", m, n);
     if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "bad type");
     InnerArgs a{};
@@ -1118,7 +1118,8 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     a.E = E_dev;
     a.Y = Y_dev;
     a.m = m; a.n = n; a.ttype = (int)type;
-    for (int k = 0; k < PMAX; ++k) a.tau[k] = k < (int)type ? tau[k] : 0.0;
+    a.use_q = tau ? 1 : 0;
+    for (int k = 0; k < PMAX; ++k) a.tau[k] = (tau && k < (int)type) ? tau[k] : 0.0;
     a.mu0 = mu0;
     a.out = ctx->step_out_dev;
     CUDA_TRY(launch_inner_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
@@ -1133,6 +1134,57 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     if (c1_out) *c1_out = o.c1;
     if (c2_out) *c2_out = o.c2;
     if (mu_out) *mu_out = o.mu;
+    return TILT_OK;
+}
+
+int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m, int n, int p,
+                   const tilt_params* params, double mu0, float* A_dev, float* E_dev, float* Y_dev, int* iters_out,
+                   double* dtau_out, double* residual_out, int* sweeps_out) {
+    if (!ctx || !D_dev || (p > 0 && !J_dev) || !A_dev || !E_dev || !Y_dev) return fail(TILT_E_INVAL, "null argument");
+    if (m < 2 || n < 2 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "window %d x %d", m, n);
+    if (p < 0 || p > PMAX) return fail(TILT_E_INVAL, "p = %d outside 0..%d", p, PMAX);
+    const Params prm = to_params(params);
+    if (!(prm.rho0 > 1.0) || !(prm.eps1 > 0.0) || prm.max_inner < 1 || !std::isfinite(prm.lam) || !std::isfinite(mu0))
+        return fail(TILT_E_INVAL, "ADM parameters out of range (rho0 > 1, eps1 > 0, max_inner >= 1)");
+    const Dims d = make_dims(m, n, p);
+    const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
+    AdmArgs a{};
+    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+    const size_t nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
+    const size_t need = sizeof(float) * (nz + (a.smem_svd ? 0 : (2 * nb + nv)));
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    float* s = reinterpret_cast<float*>(ctx->scratch);
+    a.Zg = s;
+    if (!a.smem_svd) {
+        a.Bg = a.Zg + nz;
+        a.Vg = a.Bg + nb;
+        a.Tg = a.Vg + nv;
+    }
+    a.D = D_dev;
+    a.J = J_dev;
+    a.A = A_dev;
+    a.E = E_dev;
+    a.Y = Y_dev;
+    a.m = m; a.n = n; a.p = p;
+    a.lam = prm.lam > 0.0 ? prm.lam : 1.0 / std::sqrt((double)std::max(m, n));
+    a.tol = prm.eps1;
+    a.rho = prm.rho0;
+    a.mu0 = mu0;
+    a.max_iter = prm.max_inner;
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_adm_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    const StepOut& o = *ctx->step_out;
+    if (o.status == -2) return fail(TILT_E_INVAL, "J^T J is singular");
+    if (o.status == -5) return fail(TILT_E_TIMEOUT, "a tensor-core product did not complete");
+    if (iters_out) *iters_out = o.iters;
+    if (sweeps_out) *sweeps_out = o.sweeps;
+    if (dtau_out)
+        for (int k = 0; k < p; ++k) dtau_out[k] = o.dtau[k];
+    if (residual_out) *residual_out = o.c1;
     return TILT_OK;
 }
 

@@ -133,6 +133,7 @@ struct Scratch {
     double jd[PMAX];           // J^T D_hat
     double ja[PMAX];           // J^T A
     double je[PMAX];           // J^T E
+    double jy[PMAX];           // J^T Y (the ADM baseline)
     double cvec[PMAX];         // coefficients c = G^-1 J^T (.) of the current W^T W product
     double tau[PMAX];
     double dtau[PMAX];
@@ -452,9 +453,10 @@ __device__ inline void gram_index(int q, int& a, int& b) {
 
 // G = J^T J + Q^T Q, G^-1, J^T D_hat and ||D_hat||^2, d0 = ||W^T W D_hat||_F (FP64; the
 // 45 products are reduced in three passes of 15 to keep the per-thread accumulators few).
-// Returns false when G is singular.  Results in sc->G, sc->Gi, sc->Q, sc->jd, scal[1] (d0).
+// Returns false when G is singular.  Results in sc->G, sc->Gi, sc->Q, sc->jd, scal[1] (d0),
+// scal[2] (||D_hat||^2).  use_q = false: no constraint rows (Q = 0, G = J^T J; tau unused).
 static __device__ bool k5_gram(const Dims& d, int ttype, const double* tau, const float* __restrict__ Dhat,
-                               const float* __restrict__ J, Scratch* sc) {
+                               const float* __restrict__ J, Scratch* sc, bool use_q = true) {
     const int p = d.p, S = d.S;
     constexpr int NPROD = 45, CH = 15;
     double tot[NPROD];
@@ -481,7 +483,10 @@ static __device__ bool k5_gram(const Dims& d, int ttype, const double* tau, cons
     }
     __shared__ int ok_s;
     if (threadIdx.x == 0) {
-        constraint_rows(tau, ttype, d.m, d.n, p, sc->Q);
+        if (use_q)
+            constraint_rows(tau, ttype, d.m, d.n, p, sc->Q);
+        else
+            for (int k = 0; k < 3 * PMAX; ++k) sc->Q[k] = 0.0;
         double JJ[PMAX][PMAX];
         for (int q = 0; q < 36; ++q) {
             int a, b;

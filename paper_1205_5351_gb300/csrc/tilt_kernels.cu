@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
         for (int e = threadIdx.x; e < d.S; e += NT) a.Mp[e] = 0.f;
     }
     __syncthreads();
-    if (!k5_gram(d, a.ttype, a.tau, a.Dhat, a.J, L.sc)) {
+    if (!k5_gram(d, a.ttype, a.tau, a.Dhat, a.J, L.sc, a.use_q != 0)) {
         if (threadIdx.x == 0) a.out->status = -2;
         tc_teardown(&L.sc->tc, TC_TMEM_COLS);
         return;
@@ -246,6 +246,53 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     tc_teardown(&L.sc->tc, TC_TMEM_COLS);
 }
 
+// The ADM of Zhang et al. (the comparison method of Sec. 2.2) on one problem: D, J given.
+__global__ void __launch_bounds__(NT, 1) adm_step_kernel(AdmArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    tc_setup(&L.sc->tc, TC_TMEM_COLS);
+    const Dims d = make_dims(a.m, a.n, a.p);
+    SvdBufs buf;
+    if (a.smem_svd) {
+        buf.B = L.svd;
+        buf.V = buf.B + (size_t)d.ldb * d.Cp;
+        buf.T = buf.V + (size_t)d.ldv * d.Cp;
+        buf.stage = reinterpret_cast<unsigned char*>(buf.T + (size_t)d.ldb * d.Cp);
+    } else {
+        buf.B = a.Bg;
+        buf.V = a.Vg;
+        buf.T = a.Tg;
+        buf.stage = reinterpret_cast<unsigned char*>(L.svd);
+    }
+    buf.Z = a.Zg;
+    buf.nbuf = 1;
+    buf.tc = use_tc_products(d);
+    {
+        const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+        for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }
+        for (size_t e = threadIdx.x; e < nv; e += NT) buf.V[e] = 0.f;
+    }
+    __syncthreads();
+    if (!k5_gram(d, 0, nullptr, a.D, a.J, L.sc, false)) {
+        if (threadIdx.x == 0) a.out->status = -2;
+        tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+        return;
+    }
+    double mu0 = a.mu0;
+    if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(a.D, d, L.sigma, L.w, L.sc);
+    const AdmOut o = k_inner_adm<4, true>(d, a.lam, a.tol, a.rho, mu0, a.max_iter, a.D, a.J, a.A, a.E, a.Y, buf, L,
+                                          default_schedule(d.R, d.C));
+    if (threadIdx.x == 0) {
+        a.out->status = o.tc_timeout ? -5 : o.bad ? -1 : (o.converged ? 0 : 2);
+        a.out->iters = o.iters;
+        a.out->sweeps = o.sweeps;
+        a.out->c1 = o.residual;
+        a.out->mu = o.mu_last;
+        for (int k = 0; k < PMAX; ++k) a.out->dtau[k] = k < a.p ? L.sc->dtau[k] : 0.0;
+    }
+    tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+}
+
 cudaError_t configure_kernels(size_t max_smem) {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(solver_kernel<1, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -262,6 +309,8 @@ cudaError_t configure_kernels(size_t max_smem) {
     if ((e = cudaFuncSetAttribute(worker_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
     if ((e = cudaFuncSetAttribute(inner_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(adm_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
         return e;
     return cudaSuccess;
 }
@@ -300,6 +349,11 @@ cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st) {
 
 cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st) {
     inner_step_kernel<<<1, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adm_step(const AdmArgs& a, size_t smem, cudaStream_t st) {
+    adm_step_kernel<<<1, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
 

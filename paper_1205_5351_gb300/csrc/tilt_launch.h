@@ -64,9 +64,25 @@ struct InnerArgs {
     float* Tg;
     float* Zg;     // scratch C * C
     int m, n, ttype, smem_svd;
+    int use_q;     // 0: no constraint rows (G = J^T J, W^T W = J_perp)
     double tau[PMAX];
     Params prm;
     double mu0;
+    StepOut* out;
+};
+
+struct AdmArgs {
+    const float* D;
+    const float* J;    // p planes (p may be 0)
+    float* A;
+    float* E;
+    float* Y;
+    float* Bg;         // global SVD buffers when !smem_svd
+    float* Vg;
+    float* Tg;
+    float* Zg;         // scratch C * Cp
+    int m, n, p, smem_svd, max_iter;
+    double lam, tol, rho, mu0;
     StepOut* out;
 };
 
@@ -94,6 +110,7 @@ cudaError_t launch_warp_step(const WarpArgs& a, cudaStream_t st);
 cudaError_t launch_gram_step(const GramArgs& a, cudaStream_t st);
 cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st);
+cudaError_t launch_adm_step(const AdmArgs& a, size_t smem, cudaStream_t st);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t configure_kernels(size_t max_smem);
 

@@ -36,6 +36,114 @@ __device__ inline float soft(float x, float eps) {
     return a > 0.f ? copysignf(a, x) : 0.f;
 }
 
+struct SvtStepOut {
+    int sweeps;
+    bool warm, tc_timeout;
+    unsigned long long t_svd_end;   // clock at the end of the SVD (start of the reconstruction)
+};
+
+// Singular value thresholding of the iteration's M (in buf.T): the one-sided Jacobi SVD,
+// warm-started from V when one exists, the gate allows and V has not drifted (a6), then
+// A' = S_eps(M) by the left-factor reconstruction (a7), stored into A with ||A' - A||^2 in
+// scal[7] and J^T A' in ja[] (FP64 totals of FP32 partials).  All threads.
+template <int NCH, bool TCP>
+static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& buf, const SmemLayout& L, bool& haveV, bool gate_ok,
+                                      float eps, float* __restrict__ A, const float* __restrict__ J, int jsched) {
+    Scratch* sc = L.sc;
+    const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
+    SvtStepOut so;
+    so.sweeps = 0;
+    so.warm = false;
+    so.tc_timeout = false;
+    bool warm = haveV && gate_ok;
+    if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
+    if (warm) {
+        if (TCP && buf.tc) {
+            if (!warm_start_tc(buf.T, ldb, buf.V, ldv, buf.B, C, buf.stage, buf.nbuf, &sc->tc)) {
+                so.tc_timeout = true;
+                so.t_svd_end = clk();
+                return so;
+            }
+        } else {
+            gemm_TV<NCH >= 4 ? 8 : 4>(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
+        }
+    } else {
+        for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
+        set_identity(buf.V, ldv, Cp);
+    }
+    so.warm = warm;
+    so.sweeps = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
+                               jsched_width(jsched), jsched_order(jsched));
+    haveV = true;
+    svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
+    so.t_svd_end = clk();
+    // A' = sum_kept w_k b_k v_k^T
+    const int nk = sc->iscal[1];
+    bool tc_ok = true;
+    if (TCP && buf.tc)
+        tc_ok = svt_coeffs_tc(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp, buf.stage,
+                              buf.nbuf, &sc->tc);
+    else
+        svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp);
+    float acc[1 + PMAX];
+#pragma unroll
+    for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
+    // A' = B_K Z (R x nk times nk x C); the epilogue stores A', accumulates ||A' - A||^2
+    // and J^T A' (consecutive lanes or threads take consecutive rows: the A and J
+    // accesses are coalesced)
+    auto upd = [&](int r, int c, float sa) {
+        const int e = c * R + r;
+        const float da = sa - A[e];
+        acc[0] = fmaf(da, da, acc[0]);
+        A[e] = sa;
+#pragma unroll
+        for (int k2 = 0; k2 < PMAX; ++k2)
+            if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+    };
+    if (TCP && nk > 0 && buf.tc && tc_ok) {
+        const float* Bb = buf.B;
+        const float* Zb = buf.Z;
+        const int* kept = L.kept;
+        auto la = [=](int r, int q) { return Bb[(size_t)kept[q] * ldb + r]; };
+        auto lb = [=](int q, int c) { return Zb[(size_t)q * Cp + c]; };
+        tc_ok = tc_gemm<NT, false, false>(R, C, nk, la, lb, upd, buf.stage, TC_KC, buf.nbuf, &sc->tc);
+    } else if (nk > 0 && !(TCP && buf.tc)) {
+        // one row of four columns per thread: a float4 of Z (rows at stride Cp, a
+        // broadcast) feeds four FMAs
+        const int nc4 = Cp >> 2;
+        for (int idx = threadIdx.x; idx < R * nc4; idx += NT) {
+            const int c4 = idx / R, r = idx - c4 * R;
+            const int c0 = 4 * c4;
+            float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < nk; ++q) {
+                const float bq = buf.B[(size_t)L.kept[q] * ldb + r];
+                const float4 z = *reinterpret_cast<const float4*>(buf.Z + (size_t)q * Cp + c0);
+                sv.x = fmaf(bq, z.x, sv.x);
+                sv.y = fmaf(bq, z.y, sv.y);
+                sv.z = fmaf(bq, z.z, sv.z);
+                sv.w = fmaf(bq, z.w, sv.w);
+            }
+            const float su[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u < C) upd(r, c0 + u, su[u]);
+        }
+    } else if (nk == 0) {
+        for (int e = threadIdx.x; e < S; e += NT) upd(e % R, e / R, 0.f);
+    }
+    if (!tc_ok) {
+        so.tc_timeout = true;
+        return so;
+    }
+    block_sum_f<1 + PMAX>(acc, sc->red);
+    if (threadIdx.x == 0) {
+        sc->scal[7] = block_total(sc->red, 0);
+        for (int k2 = 0; k2 < p; ++k2) sc->ja[k2] = block_total(sc->red, 1 + k2);
+    }
+    __syncthreads();
+    return so;
+}
+
 // The inner loop.  Entry: A, E, Y hold the warm start (Eq. warm_start), sc->G/Gi/jd/scal[1]
 // hold J^T J + Q^T Q, its inverse, J^T D_hat and d0 = ||W^T W D_hat||_F (k5_gram).
 // Exit: A, E, Y the result; sc->cvec = G^-1 J^T (A + E - D_hat), i.e. dtau (Eq. Delta_tau).
@@ -146,107 +254,27 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
     __syncthreads();
     for (int k = 1; k <= prm.max_inner; ++k) {
         out.iters = k;
-        // ---- a6: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate)
+        // ---- a6 + a7: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate);
+        // A' = S_{1/mu}(M); ||A' - A||^2 -> scal[7]; J^T A' -> ja
         t0 = clk();
-        bool warm = haveV && sc->iscal[6];
-        if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
-        if (warm) {
-            if (TCP && buf.tc) {
-                if (!warm_start_tc(buf.T, ldb, buf.V, ldv, buf.B, C, buf.stage, buf.nbuf, &sc->tc)) {
-                    out.bad = out.tc_timeout = true;
-                    break;
-                }
-            } else {
-                gemm_TV<NCH >= 4 ? 8 : 4>(buf.T, ldb, buf.V, ldv, buf.B, Cp, C);
-            }
-            out.warm++;
-        } else {
-            for (int e = threadIdx.x; e < ldb * Cp; e += NT) buf.B[e] = buf.T[e];
-            set_identity(buf.V, ldv, Cp);
-        }
-        const int sw = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
-                                      jsched_width(jsched), jsched_order(jsched));
-        haveV = true;
-        out.sweeps += sw;
-        const float eps = sc->fs[FS_IMU];
-        svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
-        unsigned long long t1 = clk();
+        const SvtStepOut so = svt_into<NCH, TCP>(d, buf, L, haveV, sc->iscal[6] != 0, sc->fs[FS_IMU], A, J, jsched);
+        const unsigned long long t1 = so.t_svd_end;
         if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
-
-        // ---- a7: A' = sum_kept w_k b_k v_k^T; ||A' - A||^2; J^T A'
-        const int nk = sc->iscal[1];
+        if (so.warm) out.warm++;
+        out.sweeps += so.sweeps;
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
-        bool tc_ok = true;
-        if (TCP && buf.tc)
-            tc_ok = svt_coeffs_tc(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp, buf.stage,
-                                  buf.nbuf, &sc->tc);
-        else
-            svt_coeffs_tiled(buf.T, ldb, buf.B, ldb, R, C, L.sigma, L.w, L.kept, nk, buf.Z, Cp);
-        {
-            float acc[1 + PMAX];
-#pragma unroll
-            for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
-            // A' = B_K Z (R x nk times nk x C); the epilogue stores A', accumulates ||A' - A||^2
-            // and J^T A' (consecutive lanes or threads take consecutive rows: the A and J
-            // accesses are coalesced)
-            auto upd = [&](int r, int c, float sa) {
-                const int e = c * R + r;
-                const float da = sa - A[e];
-                acc[0] = fmaf(da, da, acc[0]);
-                A[e] = sa;
-#pragma unroll
-                for (int k2 = 0; k2 < PMAX; ++k2)
-                    if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
-            };
-            if (TCP && nk > 0 && buf.tc && tc_ok) {
-                const float* Bb = buf.B;
-                const float* Zb = buf.Z;
-                const int* kept = L.kept;
-                auto la = [=](int r, int q) { return Bb[(size_t)kept[q] * ldb + r]; };
-                auto lb = [=](int q, int c) { return Zb[(size_t)q * Cp + c]; };
-                tc_ok = tc_gemm<NT, false, false>(R, C, nk, la, lb, upd, buf.stage, TC_KC, buf.nbuf, &sc->tc);
-            } else if (nk > 0 && !(TCP && buf.tc)) {
-                // one row of four columns per thread: a float4 of Z (rows at stride Cp, a
-                // broadcast) feeds four FMAs
-                const int nc4 = Cp >> 2;
-                for (int idx = threadIdx.x; idx < R * nc4; idx += NT) {
-                    const int c4 = idx / R, r = idx - c4 * R;
-                    const int c0 = 4 * c4;
-                    float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int q = 0; q < nk; ++q) {
-                        const float bq = buf.B[(size_t)L.kept[q] * ldb + r];
-                        const float4 z = *reinterpret_cast<const float4*>(buf.Z + (size_t)q * Cp + c0);
-                        sv.x = fmaf(bq, z.x, sv.x);
-                        sv.y = fmaf(bq, z.y, sv.y);
-                        sv.z = fmaf(bq, z.z, sv.z);
-                        sv.w = fmaf(bq, z.w, sv.w);
-                    }
-                    const float su[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (c0 + u < C) upd(r, c0 + u, su[u]);
-                }
-            } else if (nk == 0) {
-                for (int e = threadIdx.x; e < S; e += NT) upd(e % R, e / R, 0.f);
-            }
-            if (!tc_ok) {
-                out.bad = out.tc_timeout = true;
-                break;
-            }
-            block_sum_f<1 + PMAX>(acc, sc->red);
-            if (threadIdx.x == 0) {
-                sc->scal[7] = block_total(sc->red, 0);
-                double v[PMAX];
-                for (int k2 = 0; k2 < p; ++k2) {
-                    sc->ja[k2] = block_total(sc->red, 1 + k2);
-                    v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
-                }
-                ginv_apply(sc, p, v, sc->cvec);                       // c'
-                for (int k2 = 0; k2 < PMAX; ++k2) sc->fs[FS_CC + k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
-            }
-            __syncthreads();
+        if (so.tc_timeout) {
+            out.bad = out.tc_timeout = true;
+            break;
         }
+        if (threadIdx.x == 0) {
+            double v[PMAX];
+            for (int k2 = 0; k2 < p; ++k2) v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2];
+            ginv_apply(sc, p, v, sc->cvec);                           // c'
+            for (int k2 = 0; k2 < PMAX; ++k2) sc->fs[FS_CC + k2] = k2 < p ? (float)sc->cvec[k2] : 0.f;
+        }
+        __syncthreads();
         unsigned long long t2 = clk();
         if (threadIdx.x == 0) cyc->cyc_recon += t2 - t1;
 
@@ -371,6 +399,156 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             out.converged = true;
             break;
         }
+    }
+    return out;
+}
+
+struct AdmOut {
+    int iters, sweeps, warm;
+    bool converged, bad, tc_timeout;
+    double residual, mu_last;
+};
+
+// The ADM of Zhang et al. for the inner loop (Sec. 2.2, the comparison method): minimise the
+// augmented Lagrangian of Eq. TILT_3 over A, E and dtau in turn, then update Y and mu:
+//   A'    = S_{1/mu}(D + J dtau - E + Y/mu)
+//   E'    = T_{lam/mu}(D + J dtau - A' + Y/mu)
+//   dtau' = G^-1 J^T (A' + E' - D - Y/mu)            (G = J^T J, no constraint rows)
+//   R = D + J dtau' - A' - E';  Y' = Y + mu R;  stop when ||R|| / ||D|| < tol;  mu <- rho mu
+// from A = D, E = 0, dtau = 0, Y = 0.  Entry: sc->G/Gi/jd and scal[2] = ||D||^2 from
+// k5_gram(use_q = false).  The SVT is the same one-sided Jacobi + left-factor reconstruction
+// as LADMAP's (svt_into); J dtau is formed per pixel from the p planes.  Exit: A, E, Y,
+// sc->dtau.
+template <int NCH, bool TCP>
+static __device__ AdmOut k_inner_adm(const Dims& d, double lam, double tol, double rho, double mu0, int max_iter,
+                                     const float* __restrict__ D, const float* __restrict__ J, float* __restrict__ A,
+                                     float* __restrict__ E, float* __restrict__ Y, SvdBufs buf, const SmemLayout& L,
+                                     int jsched) {
+    Scratch* sc = L.sc;
+    const int p = d.p, S = d.S, R = d.R, ldb = d.ldb;
+    AdmOut out;
+    out.iters = out.sweeps = out.warm = 0;
+    out.converged = out.bad = out.tc_timeout = false;
+    out.residual = 0.0;
+    out.mu_last = mu0;
+    const double nD = sc->scal[2] > 0.0 ? sqrt(sc->scal[2]) : 1.0;
+    // A_0 = D, E_0 = 0, Y_0 = 0, dtau_0 = 0; the first M = D
+    for (int e = threadIdx.x; e < S; e += NT) {
+        const float dv = D[e];
+        A[e] = dv;
+        E[e] = 0.f;
+        Y[e] = 0.f;
+        buf.T[(size_t)(e / R) * ldb + (e % R)] = dv;
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < PMAX; ++k) { sc->dtau[k] = 0.0; sc->jy[k] = 0.0; sc->fs[FS_CC + k] = 0.f; }
+        sc->scal[12] = mu0;
+        sc->fs[FS_IMU] = (float)(1.0 / mu0);
+        sc->fs[FS_THR] = (float)(lam / mu0);
+        sc->fs[FS_MU] = (float)mu0;
+    }
+    __syncthreads();
+    bool haveV = false;
+    for (int k = 1; k <= max_iter; ++k) {
+        out.iters = k;
+        // A' = S_{1/mu}(M), J^T A' -> ja
+        const SvtStepOut so = svt_into<NCH, TCP>(d, buf, L, haveV, true, sc->fs[FS_IMU], A, J, jsched);
+        if (so.warm) out.warm++;
+        out.sweeps += so.sweeps;
+        if (so.tc_timeout) {
+            out.bad = out.tc_timeout = true;
+            break;
+        }
+        const float imu = sc->fs[FS_IMU], thr = sc->fs[FS_THR], muf = sc->fs[FS_MU];
+        // E' = T_{lam/mu}(D + J dtau - A' + Y/mu); J^T E'
+        {
+            float cc[PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = sc->fs[FS_CC + k2];
+            float acc[PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < PMAX; ++k2) acc[k2] = 0.f;
+            for (int e = threadIdx.x; e < S; e += NT) {
+                float jv[PMAX];
+                float jd = 0.f;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) {
+                    jv[k2] = k2 < p ? J[(size_t)k2 * S + e] : 0.f;
+                    jd = fmaf(jv[k2], cc[k2], jd);
+                }
+                const float en = soft((D[e] + jd - A[e]) + Y[e] * imu, thr);
+                E[e] = en;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) acc[k2] = fmaf(jv[k2], en, acc[k2]);
+            }
+            block_sum_f<PMAX>(acc, sc->red);
+            if (threadIdx.x == 0) {
+                // dtau' = G^-1 J^T (A' + E' - D - Y/mu)
+                const double imu64 = 1.0 / sc->scal[12];
+                double v[PMAX];
+                for (int k2 = 0; k2 < p; ++k2) {
+                    sc->je[k2] = block_total(sc->red, k2);
+                    v[k2] = sc->ja[k2] + sc->je[k2] - sc->jd[k2] - sc->jy[k2] * imu64;
+                }
+                ginv_apply(sc, p, v, sc->dtau);
+                for (int k2 = 0; k2 < PMAX; ++k2) sc->fs[FS_CC + k2] = k2 < p ? (float)sc->dtau[k2] : 0.f;
+                const double mu_next = rho * sc->scal[12];
+                sc->fs[FS_IMUN] = (float)(1.0 / mu_next);
+            }
+            __syncthreads();
+        }
+        // R = D + J dtau' - A' - E'; Y' = Y + mu R; ||R||^2; J^T Y'; next M = D + J dtau' - E' + Y'/(rho mu)
+        {
+            float cc[PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < PMAX; ++k2) cc[k2] = sc->fs[FS_CC + k2];
+            const float imun = sc->fs[FS_IMUN];
+            float acc[1 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
+            for (int e = threadIdx.x; e < S; e += NT) {
+                float jv[PMAX];
+                float jd = 0.f;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) {
+                    jv[k2] = k2 < p ? J[(size_t)k2 * S + e] : 0.f;
+                    jd = fmaf(jv[k2], cc[k2], jd);
+                }
+                const float dj = D[e] + jd;
+                const float ee = E[e];
+                const float r = (dj - A[e]) - ee;
+                const float y = fmaf(muf, r, Y[e]);
+                Y[e] = y;
+                acc[0] = fmaf(r, r, acc[0]);
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2) acc[1 + k2] = fmaf(jv[k2], y, acc[1 + k2]);
+                buf.T[(size_t)(e / R) * ldb + (e % R)] = (dj - ee) + y * imun;
+            }
+            block_sum_f<1 + PMAX>(acc, sc->red);
+            if (threadIdx.x == 0) {
+                const double res = sqrt(block_total(sc->red, 0)) / nD;
+                sc->scal[15] = res;
+                for (int k2 = 0; k2 < p; ++k2) sc->jy[k2] = block_total(sc->red, 1 + k2);
+                int ctl = LOOP_GO;
+                if (!isfinite(res)) ctl = LOOP_BAD;
+                else if (res < tol) ctl = LOOP_CONVERGED;
+                sc->iscal[5] = ctl;
+                sc->scal[16] = sc->scal[12];
+                if (ctl == LOOP_GO) {
+                    const double mu_next = rho * sc->scal[12];
+                    sc->scal[12] = mu_next;
+                    sc->fs[FS_IMU] = (float)(1.0 / mu_next);
+                    sc->fs[FS_THR] = (float)(lam / mu_next);
+                    sc->fs[FS_MU] = (float)mu_next;
+                }
+            }
+            __syncthreads();
+        }
+        const int ctl = sc->iscal[5];
+        out.residual = sc->scal[15];
+        out.mu_last = sc->scal[16];
+        if (ctl == LOOP_BAD) { out.bad = true; break; }
+        if (ctl == LOOP_CONVERGED) { out.converged = true; break; }
     }
     return out;
 }

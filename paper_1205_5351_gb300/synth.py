@@ -267,6 +267,52 @@ def multistart_batch(count: int = 64, first: int = 0, side: int = 512) -> list[P
     return out
 
 
+# Range-of-convergence grid of Sec. 6.2: rotation 0 .. pi/6 in steps of pi/60, skew 0 .. 1 in
+# steps of 0.05.
+CONVERGENCE_THETAS = tuple(3.0 * i for i in range(11))
+CONVERGENCE_SKEWS = tuple(round(0.05 * j, 2) for j in range(21))
+
+
+def convergence_grid(count: int | None = None, first: int = 0, side: int = 60, period: float = 12.0) -> list[Patch]:
+    """Checkerboards deformed by A(theta, t) = R(theta) [[1, t], [0, 1]] over the grid of
+    CONVERGENCE_THETAS x CONVERGENCE_SKEWS (patch index = theta index * 21 + skew index), each
+    to be rectified from the identity (the range-of-convergence experiment, Sec. 6.2)."""
+    total = len(CONVERGENCE_THETAS) * len(CONVERGENCE_SKEWS)
+    count = total - first if count is None else count
+    out = []
+    for idx in range(first, first + count):
+        i, j = divmod(idx % total, len(CONVERGENCE_SKEWS))
+        rng = np.random.default_rng(seed_for(5, idx))
+        p = make_patch(rng, side, side, kind="checker", period=period, theta_deg=CONVERGENCE_THETAS[i],
+                       skew=CONVERGENCE_SKEWS[j], ttype=AFFINE)
+        p.meta["grid"] = (i, j)
+        out.append(p)
+    return out
+
+
+# Corruption levels of the robustness experiment of Sec. 6.2: 0 .. 100 % in steps of 5 %.
+CORRUPTION_LEVELS = tuple(round(0.05 * i, 2) for i in range(21))
+
+
+def corruption_sweep(count: int | None = None, first: int = 0, textures: int = 10, side: int = 60) -> list[Patch]:
+    """Rank-3 textures rotated by 10 degrees with a fraction of their pixels replaced by
+    Uniform[0, 1] values, every level of CORRUPTION_LEVELS for each of ``textures`` textures
+    (patch index = texture * 21 + level index; the robustness experiment, Sec. 6.2).  A
+    texture draws the same random numbers at every level, so its corrupted pixel sets are
+    nested as the level grows."""
+    total = textures * len(CORRUPTION_LEVELS)
+    count = total - first if count is None else count
+    out = []
+    for idx in range(first, first + count):
+        k, lv = divmod(idx % total, len(CORRUPTION_LEVELS))
+        rng = np.random.default_rng(seed_for(6, k))
+        p = make_patch(rng, side, side, kind="lowrank", rank=3, theta_deg=10.0,
+                       corruption=CORRUPTION_LEVELS[lv], ttype=AFFINE)
+        p.meta["sweep"] = (k, lv)
+        out.append(p)
+    return out
+
+
 def random_inner_problem(rng: np.random.Generator, m: int, n: int, p: int = 6):
     """Inputs of the inner-loop-only experiment (Sec. 6.1): D o tau with iid Uniform[0, 1]
     entries and a Jacobian with iid N(0, 1) entries (mn x p, rows in row-major pixel order)."""

@@ -97,6 +97,8 @@ SIGNATURES = {
     "tilt_inner": (_i, [_vp, _vp, _vp, _i, _i, _P(_d), _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d),
                         _P(_d), _P(_d), _P(_d)]),
     "tilt_svt_noalloc": (_i, [_vp, _i, _i, ctypes.c_float, _vp, _vp, _vp]),
+    "tilt_inner_adm": (_i, [_vp, _vp, _vp, _i, _i, _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d), _P(_d),
+                            _P(_i)]),
     "tilt_best_of": (_i, [_P(Result), _i, _i, _P(_i)]),
     "tilt_autotune": (_i, [_vp, _P(_i), _i, _i, _P(_i)]),
 }
@@ -331,9 +333,25 @@ class Context:
         _check(lib().tilt_svt(self.h, _dptr(M_t), m, n, float(eps), _dptr(A), sig, ctypes.byref(sw)), self.h)
         return A, np.array(sig, dtype=np.float32), sw.value
 
+    def inner_adm(self, D_t, J_t, m: int, n: int, p: int, params: Params | None, mu0: float = -1.0) -> dict:
+        """The ADM baseline (tilt_inner_adm); returns A, E, Y (flat CUDA tensors, long layout),
+        iterations, dtau, the last relative residual and the Jacobi sweeps."""
+        import torch
+        A = torch.empty_like(D_t)
+        E = torch.empty_like(D_t)
+        Y = torch.empty_like(D_t)
+        it, sw = ctypes.c_int(), ctypes.c_int()
+        dt = (ctypes.c_double * 8)()
+        res = ctypes.c_double()
+        _check(lib().tilt_inner_adm(self.h, _dptr(D_t), _dptr(J_t) if p else None, m, n, p,
+                                    ctypes.byref(params) if params else None, float(mu0), _dptr(A), _dptr(E),
+                                    _dptr(Y), ctypes.byref(it), dt, ctypes.byref(res), ctypes.byref(sw)), self.h)
+        return dict(A=A, E=E, Y=Y, iters=it.value, dtau=np.array(dt[:p]), residual=res.value, sweeps=sw.value)
+
     def inner(self, Dhat_t, J_t, m: int, n: int, tau, ttype: int, params: Params | None, mu0: float,
               A_t, E_t, Y_t) -> dict:
-        tau_c = (ctypes.c_double * 8)(*list(np.asarray(tau, dtype=np.float64))[:8])
+        """tilt_inner; tau = None runs without constraint rows (W^T W = J_perp)."""
+        tau_c = (ctypes.c_double * 8)(*list(np.asarray(tau, dtype=np.float64))[:8]) if tau is not None else None
         it = ctypes.c_int()
         dt = (ctypes.c_double * 8)()
         c1, c2, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -408,6 +408,26 @@ def test_table_numerical_objective(size):
     assert abs(np.mean(objs) - want) / want < 0.01
 
 
+@pytest.mark.parametrize("size", [50, 100])
+def test_ladmap_iterations_match_table_numerical(size):
+    # Table 1's LADMAP column with the tuning the paper describes (rho0 and eps2 chosen so that
+    # LADMAP stops at the ADM's objective; reading R17: rho0 = 2, eps2 = 0.1): about 21-22
+    # iterations at the printed objective
+    rows = json.load(open(os.path.join(GOLDEN, "table_numerical.json")))["rows"]
+    row = {r[0]: r for r in rows}[size]
+    objs, its = [], []
+    for trial in range(5):
+        rng = np.random.default_rng(1000 + trial)
+        D, J = synth.random_inner_problem(rng, size, size, 6)
+        D = D - 0.5
+        lam = 1 / math.sqrt(size)
+        res = O.inner_ladmap(D, J, None, lam, D, 0 * D, 0 * D, O.Params(eps1=1e-7, eps2=0.1, rho0=2.0, max_inner=2000))
+        objs.append(O.objective(res.A, res.E, lam))
+        its.append(res.iters)
+    assert abs(np.mean(objs) - row[2]) / row[2] < 0.01
+    assert abs(np.mean(its) - row[4]) / row[4] < 0.15
+
+
 # ------------------------------------------------------------------ Algorithm 1 end to end
 def _offdiag(tau, tau_true):
     L = np.array([[tau_true[0], tau_true[1]], [tau_true[3], tau_true[4]]])
