@@ -120,7 +120,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream"], default="affine")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream", "table1"], default="affine")
     ap.add_argument("--patches", type=int, default=None, help="patches per GPU (default: the workload's)")
     ap.add_argument("--plain-patches", type=int, default=8, help="patches in the plain GPU solver sample (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the oracle CPU sample")
@@ -441,7 +441,8 @@ def run_ours(args, rank, world, local_rank, dist):
             # by which patch happens to finish last
             "kcycles_per_inner_iter": round(sum(sum(r["phase_cycles"]) for r in results) / max(1, inner) / 1e3, 2),
             "svd": {"sweeps_per_svd": sum(r["svd_sweeps"] for r in results) / max(1, inner),
-                    "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner)},
+                    "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner),
+                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results)},
             "phase_split": dict(zip(["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"],
                                     [round(sum(r["phase_cycles"][i] for r in results) /
                                            max(1, sum(sum(r["phase_cycles"]) for r in results)), 4)
@@ -595,6 +596,60 @@ def run_stream(args, rank, world, local_rank):
             "gpu_launches": launches, "clocks": clk}
 
 
+# ----------------------------------------------------------------------------- Table 1 comparison
+def run_table1(args, rank):
+    """The inner-loop-only comparison of Sec. 6.1 (Table 1) on the GPU: the ADM of Zhang et al.
+    (tilt_inner_adm, rho = 1.25) against LADMAP (tilt_inner without constraint rows, Table 1's
+    tuning rho0 = 2, eps2 = 0.1), both to 1e-5 on the same random D o tau ~ U[-1/2, 1/2] and
+    J ~ N(0, 1) (p = 6, lambda = 1/sqrt(n)), 10 trials per size; one CTA per solve, timed with
+    CUDA events around each call."""
+    import numpy as np
+    import torch
+
+    from paper_1205_5351_gb300 import synth, tilt
+    if rank != 0:
+        return None
+    torch.cuda.set_device(0)
+    ctx = tilt.Context(0)
+    rows = []
+    for size in (10, 50, 100, 300, 500):
+        acc = {"adm": [], "ladmap": []}
+        for trial in range(10):
+            rng = np.random.default_rng(1000 + trial)
+            D, J = synth.random_inner_problem(rng, size, size, 6)
+            D = (D - 0.5).astype(np.float32)
+            D_t = torch.from_numpy(tilt.to_long_layout(D)).cuda()
+            J_t = torch.from_numpy(tilt.jacobian_from_rows(J.astype(np.float32), size, size)).cuda()
+            lam = 1 / math.sqrt(size)
+            mu0 = 1.25 / float(np.linalg.norm(D.astype(np.float64), 2))
+            for name in ("adm", "ladmap"):
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record()
+                if name == "adm":
+                    r = ctx.inner_adm(D_t, J_t, size, size, 6, tilt.default_params(rho0=1.25, eps1=1e-5), mu0)
+                    A, E, it = r["A"], r["E"], r["iters"]
+                else:
+                    A, E, Y = D_t.clone(), torch.zeros_like(D_t), torch.zeros_like(D_t)
+                    r = ctx.inner(D_t, J_t, size, size, None, 6,
+                                  tilt.default_params(rho0=2.0, eps2=0.1, eps1=1e-5, max_inner=2000), mu0, A, E, Y)
+                    it = r["iters"]
+                ev1.record()
+                torch.cuda.synchronize()
+                Ah = tilt.from_long_layout(A.cpu().numpy(), size, size).astype(np.float64)
+                Eh = tilt.from_long_layout(E.cpu().numpy(), size, size).astype(np.float64)
+                obj = float(np.linalg.svd(Ah, compute_uv=False).sum() + lam * np.abs(Eh).sum())
+                acc[name].append((ev0.elapsed_time(ev1), it, obj))
+        rows.append({"size": size, **{k: {"ms": statistics.mean(x[0] for x in v), "iters": statistics.mean(x[1] for x in v),
+                                            "objective": statistics.mean(x[2] for x in v)} for k, v in acc.items()}})
+    ctx.close()
+    return {"metric": "inner-loop solve time, ADM of Zhang et al. vs LADMAP (Table 1 setting)", "value": None,
+            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Table 1: random D o tau ~ U[-1/2, 1/2], J ~ N(0, 1), p = 6, lambda = 1/sqrt(n), "
+                                   "10 trials per size, tolerance 1e-5 for both methods"},
+            "rows": rows}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -648,6 +703,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "stream":
         out = run_stream(args, rank, world, local_rank)
+    elif args.workload == "table1":
+        out = run_table1(args, rank)
     else:
         out = run_ours(args, rank, world, local_rank, dist)
     if rank == 0 and out is not None:

@@ -105,7 +105,8 @@ typedef struct {
     int outer_iters;     /* outer steps taken                                                 */
     int inner_iters;     /* inner iterations summed over outer steps                          */
     int svd_sweeps;      /* one-sided Jacobi sweeps summed over all SVDs                      */
-    int svd_warm;        /* SVDs that started from the previous right singular vectors        */
+    int svd_warm;        /* SVDs that started from the previous right singular vectors (all but
+                            the first of a solve)                                            */
     int oob_pixels;      /* samples clamped to the image edge in the last warp                */
     double kkt_residual; /* last Eq. Cond1 value                                              */
     float latency_ms;    /* submit -> completion, host clock                                  */
@@ -119,6 +120,9 @@ typedef struct {
                             SM with the tensor-core products (short side >= 160), or with
                             every SVD buffer in device memory.  -1: solved by the persistent
                             workers                                                         */
+    int svd_reorth;      /* warm starts whose right singular vectors had drifted from
+                            orthogonal (a column norm off by more than 1e-4) and were
+                            re-orthonormalised in FP64 first                                */
 } tilt_result;
 
 /* Fill *p with the default parameters. */
@@ -234,6 +238,17 @@ int tilt_gram(tilt_ctx* ctx, const float* J_dev, int m, int n, const double* tau
  * NULL) the singular values of M in no particular order; *sweeps_out the sweeps used. */
 int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* A_dev,
              float* sigma_out, int* sweeps_out);
+
+/* tilt_svt warm-started as the solver warm-starts every SVD after the first (Sec. 5): from the
+ * right singular vectors V of the previous iteration's M, re-orthonormalised first in FP64
+ * (modified Gram-Schmidt) when a column norm of V is off by more than 1e-4 (FP32 rotations
+ * let V drift from orthogonal), then B = X V and one-sided Jacobi sweeps from there.  X is
+ * the m x n matrix M_dev when m >= n, its transpose otherwise (the long-side layout above);
+ * V_dev: device, min(m, n) x min(m, n), column-major with stride min(m, n); on return it holds
+ * the new right singular vectors of X.  *reorth_out (may be NULL) = 1 when V was
+ * re-orthonormalised.  Other arguments and errors as tilt_svt. */
+int tilt_svt_warm(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* V_dev, float* A_dev,
+                  float* sigma_out, int* sweeps_out, int* reorth_out);
 
 /* The inner loop of Algorithm 1 (Eqs. A, E, Y, mu, rho, Cond1, Cond2 in the W^T W form of
  * Eq. newvars2) on given D_hat, J and tau (tau gives Q; tau = NULL: no constraint rows, so

@@ -269,6 +269,15 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
     L.vg = (place & 2) ? 0 : take(nv);
     L.tg = (place & 4) ? 0 : take(nb);
     L.jsched = jsched_for(ctx, d.R, d.C);
+    if (place == 0) {
+        // B and V in device memory: staged sweeps, their column blocks sharing the stage region
+        // with the tensor-core products (the two are never in use at once)
+        const int bw = staged_block(d, ctx->max_smem - head);
+        if (bw > 0) {
+            L.jsched = bw | JSCHED_STAGED;
+            L.smem = head + std::max(L.smem - head, jacobi_stage_bytes(d, bw));
+        }
+    }
     // the C x C SVT coefficients too, where they fit without changing the occupancy class
     // (bit 3); else they stay in the workspace
     {
@@ -479,6 +488,7 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->phase_cycles[3] = r.cyc_elem;
     out->phase_cycles[4] = r.cyc_other;
     out->launch_class = t.batch < 0 ? -1 : t.klass;
+    out->svd_reorth = r.svd_reorth;
 }
 
 // Copy the device planes A and E (long-side-contiguous) to host m x n row-major arrays (either
@@ -522,6 +532,24 @@ int ensure_scratch(tilt_ctx* ctx, size_t bytes) {
     CUDA_TRY(cudaMalloc(&ctx->scratch, bytes));
     ctx->scratch_bytes = bytes;
     return TILT_OK;
+}
+
+// Jacobi schedule and dynamic shared memory of a step entry point: the SVD buffers in shared
+// memory when svd + head fits (default round-robin schedule), else in device memory with
+// staged sweeps, whose blocks share the stage region with the tensor-core products.
+void step_plan(const tilt_ctx* ctx, const Dims& d, size_t svd, size_t head_tc, int* smem_svd, int* jsched,
+               size_t* smem) {
+    const size_t head = smem_head_bytes();
+    *smem_svd = (svd + head_tc <= ctx->max_smem) ? 1 : 0;
+    *jsched = default_group_width(d.R, d.C);
+    *smem = *smem_svd ? svd + head_tc : head_tc;
+    if (!*smem_svd) {
+        const int bw = staged_block(d, ctx->max_smem - head);
+        if (bw > 0) {
+            *jsched = bw | JSCHED_STAGED;
+            *smem = head + std::max(head_tc - head, jacobi_stage_bytes(d, bw));
+        }
+    }
 }
 
 int run_step(tilt_ctx* ctx) {
@@ -1052,7 +1080,21 @@ int tilt_gram(tilt_ctx* ctx, const float* J_dev, int m, int n, const double* tau
     return TILT_OK;
 }
 
+static int svt_call(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* V_dev, float* A_dev,
+                    float* sigma_out, int* sweeps_out, int* reorth_out);
+
 int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* A_dev, float* sigma_out, int* sweeps_out) {
+    return svt_call(ctx, M_dev, m, n, eps, nullptr, A_dev, sigma_out, sweeps_out, nullptr);
+}
+
+int tilt_svt_warm(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* V_dev, float* A_dev,
+                  float* sigma_out, int* sweeps_out, int* reorth_out) {
+    if (!V_dev) return fail(TILT_E_INVAL, "null V");
+    return svt_call(ctx, M_dev, m, n, eps, V_dev, A_dev, sigma_out, sweeps_out, reorth_out);
+}
+
+static int svt_call(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* V_dev, float* A_dev,
+                    float* sigma_out, int* sweeps_out, int* reorth_out) {
     if (!ctx || !M_dev || !A_dev) return fail(TILT_E_INVAL, "null argument");
     if (m < 1 || n < 1 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "matrix %d x %d", m, n);
     if (!(eps >= 0.f)) return fail(TILT_E_INVAL, "eps must be >= 0");
@@ -1062,7 +1104,8 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
     a.M = M_dev;
     a.A = A_dev;
     a.m = m; a.n = n; a.eps = eps;
-    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    size_t smem = 0;
+    step_plan(ctx, d, svd, head, &a.smem_svd, &a.jsched, &smem);
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t nz = (size_t)d.C * d.Cp;
     const size_t need = sizeof(float) * ((a.smem_svd ? 0 : (2 * nb + nv)) + MAX_SIDE + ((nz + 63) & ~(size_t)63));
@@ -1077,12 +1120,14 @@ int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* 
         a.Tg = a.Vg + nv;
     }
     a.out = ctx->step_out_dev;
-    CUDA_TRY(launch_svt_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    a.Vio = V_dev;
+    CUDA_TRY(launch_svt_step(a, smem, ctx->streams[0]));
     rc = run_step(ctx);
     if (rc) return rc;
     if (ctx->step_out->status == -5) return fail(TILT_E_TIMEOUT, "a tensor-core product did not complete");
     if (sigma_out) CUDA_TRY(cudaMemcpy(sigma_out, a.sigma, sizeof(float) * d.C, cudaMemcpyDeviceToHost));
     if (sweeps_out) *sweeps_out = ctx->step_out->sweeps;
+    if (reorth_out) *reorth_out = ctx->step_out->reorth;
     return TILT_OK;
 }
 
@@ -1097,7 +1142,8 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     if (!params_ok(a.prm)) return fail(TILT_E_INVAL, "parameters out of range");
     const Dims d = make_dims(m, n, (int)type);
     const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
-    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    size_t smem = 0;
+    step_plan(ctx, d, svd, head, &a.smem_svd, &a.jsched, &smem);
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
     const size_t need = sizeof(float) * (2 * S4 + nz + (a.smem_svd ? 0 : (2 * nb + nv)));
@@ -1122,7 +1168,7 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     for (int k = 0; k < PMAX; ++k) a.tau[k] = (tau && k < (int)type) ? tau[k] : 0.0;
     a.mu0 = mu0;
     a.out = ctx->step_out_dev;
-    CUDA_TRY(launch_inner_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    CUDA_TRY(launch_inner_step(a, smem, ctx->streams[0]));
     rc = run_step(ctx);
     if (rc) return rc;
     const StepOut& o = *ctx->step_out;
@@ -1149,7 +1195,8 @@ int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m,
     const Dims d = make_dims(m, n, p);
     const size_t svd = svd_smem_bytes(d), head = smem_head_bytes() + (use_tc_products(d) ? tc_stage_for(d, 1) : 0);
     AdmArgs a{};
-    a.smem_svd = (svd + head <= ctx->max_smem) ? 1 : 0;
+    size_t smem = 0;
+    step_plan(ctx, d, svd, head, &a.smem_svd, &a.jsched, &smem);
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
     const size_t need = sizeof(float) * (nz + (a.smem_svd ? 0 : (2 * nb + nv)));
@@ -1174,7 +1221,7 @@ int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m,
     a.mu0 = mu0;
     a.max_iter = prm.max_inner;
     a.out = ctx->step_out_dev;
-    CUDA_TRY(launch_adm_step(a, a.smem_svd ? svd + head : head, ctx->streams[0]));
+    CUDA_TRY(launch_adm_step(a, smem, ctx->streams[0]));
     rc = run_step(ctx);
     if (rc) return rc;
     const StepOut& o = *ctx->step_out;

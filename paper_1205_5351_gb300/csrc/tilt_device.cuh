@@ -34,7 +34,7 @@ struct Result {
     double tau[8];
     double objective;
     double lambda;
-    int rank_A, outer_iters, inner_iters, svd_sweeps, svd_warm, oob_pixels;
+    int rank_A, outer_iters, inner_iters, svd_sweeps, svd_warm, svd_reorth, oob_pixels;
     double kkt_residual;
     // per-phase clock counters (SM cycles), for the time split of the fused solver
     unsigned long long cyc_warp, cyc_svd, cyc_recon, cyc_elem, cyc_other;
@@ -647,10 +647,8 @@ __device__ inline float group_sum(float v, unsigned mask, int gw) {
 // One pair step of the one-sided Jacobi for columns i, j, executed by a group of gw lanes
 // (lane g of the group holds float4 chunks g, g+gw, ... ; in registers while nqb <= gw NCH).
 template <int NCH, int gw>
-__device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, int j, int nqb, int nqv, int g,
-                                   unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
-    float4* bi = reinterpret_cast<float4*>(B + (size_t)i * ldb);
-    float4* bj = reinterpret_cast<float4*>(B + (size_t)j * ldb);
+__device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, float4* vj, int nqb, int nqv, int g,
+                                        unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
     float a = 0.f, b = 0.f, gg = 0.f;
     if (in_regs) {
         float4 x[NCH], y[NCH];
@@ -689,8 +687,6 @@ __device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, 
                 }
             }
             // V (C <= R rows): the same chunk pattern, unrolled so that all loads are in flight
-            float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
-            float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
 #pragma unroll
             for (int t = 0; t < NCH; ++t) {
                 const int q = g + gw * t;
@@ -724,8 +720,6 @@ __device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, 
                 bi[q] = rot_x(x, y, rp.s, rp.r);
                 bj[q] = rot_y(x, y, rp.s, rp.r);
             }
-            float4* vi = reinterpret_cast<float4*>(V + (size_t)i * ldv);
-            float4* vj = reinterpret_cast<float4*>(V + (size_t)j * ldv);
             for (int q = g; q < nqv; q += gw) {
                 const float4 x = vi[q], y = vj[q];
                 vi[q] = rot_x(x, y, rp.s, rp.r);
@@ -735,6 +729,16 @@ __device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, 
             maxcos = fmaxf(maxcos, rp.cosabs);
         }
     }
+}
+
+template <int NCH, int gw>
+__device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, int j, int nqb, int nqv, int g,
+                                   unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
+    jacobi_pair_cols<NCH, gw>(reinterpret_cast<float4*>(B + (size_t)i * ldb),
+                              reinterpret_cast<float4*>(B + (size_t)j * ldb),
+                              reinterpret_cast<float4*>(V + (size_t)i * ldv),
+                              reinterpret_cast<float4*>(V + (size_t)j * ldv), nqb, nqv, g, gmask, tol, in_regs,
+                              rotated, maxcos);
 }
 
 // End of a sweep: did any pair rotate, and the largest rotated cosine (all threads).
@@ -861,6 +865,148 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
     return sweep;
 }
 
+// Staged sweeps for matrices whose B and V live in device memory (the largest windows):
+// the columns form blocks of b; block pairs are visited row by row (P = 0 .. NB-1, then
+// Q = P+1 .. NB-1: every column pair once per sweep, the pairs inside block P when P becomes
+// the row block).  The row block P and the current block Q sit in shared memory, brought in
+// and written back by bulk copies of whole columns (one per column of B and of V, issued by
+// thread 0); Q alternates between two buffers, so the write-back of one block overlaps the
+// work on the next.  Inside a block pair one warp rotates one column pair (32 lanes, float4
+// chunks), b disjoint pairs per sub-round and a CTA barrier between sub-rounds, so the
+// sweep reads each column of Q once per row instead of once per pair.  stage: 3 b (ldb + ldv)
+// floats; st: the bulk-copy mbarrier.  Returns the number of sweeps, or -1 when a bounded
+// wait for a copy gave up (st->error is set).
+template <int NCH>
+static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
+                                       int* flag, int b, float* stage, TcState* st) {
+    (void)R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int NB = (C + b - 1) / b;
+    const int nqb = ldb / 4, nqv = ldv / 4;
+    const bool in_regs = nqb <= 32 * NCH;
+    float* sB = stage;                               // 3 b columns of ldb floats
+    float* sV = stage + (size_t)3 * b * ldb;         // 3 b columns of ldv floats
+    auto colB = [&](int slot) { return reinterpret_cast<float4*>(sB + (size_t)slot * ldb); };
+    auto colV = [&](int slot) { return reinterpret_cast<float4*>(sV + (size_t)slot * ldv); };
+    auto ncols = [&](int blk) { return min(b, C - blk * b); };
+    // thread 0: load block blk into slots base .. base + ncols - 1 (counted on st->jbar)
+    auto load = [&](int blk, int base) {
+        const int nc = ncols(blk);
+        mbar_arrive_expect_tx(&st->jbar, (uint32_t)nc * (uint32_t)(ldb + ldv) * 4u);
+        for (int c = 0; c < nc; ++c) {
+            bulk_g2s(sB + (size_t)(base + c) * ldb, B + (size_t)(blk * b + c) * ldb, (uint32_t)ldb * 4u, &st->jbar);
+            bulk_g2s(sV + (size_t)(base + c) * ldv, V + (size_t)(blk * b + c) * ldv, (uint32_t)ldv * 4u, &st->jbar);
+        }
+    };
+    // thread 0: write block blk back from slots base ..; one bulk group
+    auto store = [&](int blk, int base) {
+        const int nc = ncols(blk);
+        for (int c = 0; c < nc; ++c) {
+            bulk_s2g(B + (size_t)(blk * b + c) * ldb, sB + (size_t)(base + c) * ldb, (uint32_t)ldb * 4u);
+            bulk_s2g(V + (size_t)(blk * b + c) * ldv, sV + (size_t)(base + c) * ldv, (uint32_t)ldv * 4u);
+        }
+        bulk_commit();
+    };
+    // all threads: wait for the loads counted on st->jbar; false when the bounded wait gave up
+    auto wait_loads = [&]() {
+        const bool ok = mbar_wait(&st->jbar, st->jphase);
+        const bool all = __syncthreads_and(ok);
+        if (threadIdx.x == 0) st->jphase ^= 1;
+        __syncthreads();
+        return all;
+    };
+    // every thread's generic writes (to B, V in device memory, or to the stage) before the
+    // bulk copies that read them
+    fence_proxy_async();
+    __syncthreads();
+    int sweep = 0;
+    bool ok = true;
+    while (sweep < max_sweeps && ok) {
+        if (threadIdx.x == 0) { flag[0] = 0; reinterpret_cast<float*>(flag)[1] = 0.f; }
+        __syncthreads();
+        bool rotated = false;
+        float maxcos = 0.f;
+        for (int P = 0; P < NB && ok; ++P) {
+            // the row block: its last copy in device memory was written by an earlier bulk store
+            if (threadIdx.x == 0) {
+                bulk_wait_all();
+                load(P, 0);
+            }
+            if (!(ok = wait_loads())) break;
+            // pairs inside block P: round-robin over b columns, b - 1 sub-rounds of b/2 pairs
+            const int nP = ncols(P);
+            for (int sr = 0; sr < b - 1; ++sr) {
+                if (warp < b / 2) {
+                    int li = 0;
+                    if (warp) { li = warp - 1 + sr; if (li >= b - 1) li -= b - 1; li += 1; }
+                    int lj = b - 2 - warp + sr;
+                    if (lj >= b - 1) lj -= b - 1;
+                    lj += 1;
+                    if (li < nP && lj < nP)
+                        jacobi_pair_cols<NCH, 32>(colB(li), colB(lj), colV(li), colV(lj), nqb, nqv, lane, 0xFFFFFFFFu,
+                                                  tol, in_regs, rotated, maxcos);
+                }
+                __syncthreads();
+            }
+            if (P + 1 < NB) {
+                if (threadIdx.x == 0) load(P + 1, b);
+                if (!(ok = wait_loads())) break;
+            }
+            int cur = b;                      // slot base of the buffer holding Q
+            for (int Q = P + 1; Q < NB; ++Q) {
+                const int nQ = ncols(Q);
+                for (int s = 0; s < b; ++s) {
+                    if (warp < b) {
+                        const int a = warp;
+                        int c = a + s;
+                        if (c >= b) c -= b;
+                        if (a < nP && c < nQ)
+                            jacobi_pair_cols<NCH, 32>(colB(a), colB(cur + c), colV(a), colV(cur + c), nqb, nqv, lane,
+                                                      0xFFFFFFFFu, tol, in_regs, rotated, maxcos);
+                    }
+                    __syncthreads();
+                }
+                fence_proxy_async();
+                __syncthreads();
+                const int other = cur == b ? 2 * b : b;
+                if (threadIdx.x == 0) {
+                    store(Q, cur);
+                    if (Q + 1 < NB) {
+                        bulk_wait_read<1>();      // the write-back of Q - 1 has left the other buffer
+                        load(Q + 1, other);
+                    }
+                }
+                if (Q + 1 < NB && !(ok = wait_loads())) break;
+                cur = other;
+            }
+            if (!ok) break;
+            fence_proxy_async();
+            __syncthreads();
+            if (threadIdx.x == 0) store(P, 0);
+        }
+        if (threadIdx.x == 0) {
+            bulk_wait_all();
+            fence_proxy_async();
+        }
+        __syncthreads();
+        if (!ok) break;
+        ++sweep;
+        if (sweep_done(rotated, maxcos, tol, flag)) break;
+    }
+    if (!ok) {
+        // a load that gave up may still be in flight: wait for it once more (bounded), and for
+        // the issued write-backs, before the stage can be reused
+        if (threadIdx.x == 0) {
+            mbar_wait(&st->jbar, st->jphase ^ 1);
+            bulk_wait_all();
+            st->error = 1;
+        }
+        __syncthreads();
+        return -1;
+    }
+    return sweep;
+}
+
 template <int NCH>
 static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
                                 int* flag, int gw, int order) {
@@ -880,8 +1026,21 @@ __host__ __device__ inline int default_group_width(int R, int C) {
 }
 
 constexpr int JSCHED_BLOCK = 256;   // schedule bit: block-cyclic pair ordering
+constexpr int JSCHED_STAGED = 512;  // schedule: staged block pairs (width field = block width b)
 __host__ __device__ inline int jsched_width(int js) { return js & 255; }
 __host__ __device__ inline int jsched_order(int js) { return js >> 8; }
+
+// Staged sweeps (matrices whose B and V live in device memory): shared-memory bytes of the
+// three column blocks of width b, and the widest even b <= 16 whose blocks fit in `avail`
+// bytes (0 when none does).
+__host__ __device__ inline size_t jacobi_stage_bytes(const Dims& d, int b) {
+    return (size_t)3 * b * (d.ldb + d.ldv) * sizeof(float);
+}
+__host__ __device__ inline int staged_block(const Dims& d, size_t avail) {
+    for (int b = 16; b >= 2; b -= 2)
+        if (jacobi_stage_bytes(d, b) <= avail) return b;
+    return 0;
+}
 
 // Schedule of a size bucket the autotuner has not timed: block-cyclic ordering (one CTA
 // barrier per block round instead of one per round), 16 lanes per pair for the long
@@ -1135,6 +1294,33 @@ static __device__ float v_drift(const float* V, int ldv, int C, Scratch* sc) {
     for (int w = 0; w < NW; ++w) r = fmaxf(r, fr[w]);
     __syncthreads();
     return r;
+}
+
+// Re-orthonormalise the C columns of V (stride ldv) by modified Gram-Schmidt in FP64 before a
+// warm start, when the FP32 rotations have let V drift from orthogonal: column j is
+// normalised, then projected out of every later column, the dot products and updates in
+// FP64 (V itself stays FP32, so the result is orthonormal to FP32 rounding).  About C^3
+// FP64 multiply-adds and 2 C CTA barriers; all threads.
+static __device__ void v_reorth_fp64(float* V, int ldv, int C, Scratch* sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < C; ++j) {
+        float* vj = V + (size_t)j * ldv;
+        double nn[1] = {0.0};
+        for (int r = threadIdx.x; r < C; r += NT) nn[0] += (double)vj[r] * (double)vj[r];
+        block_sum64<1>(nn, sc->red);
+        const double inv = nn[0] > 0.0 ? 1.0 / sqrt(nn[0]) : 0.0;
+        for (int r = threadIdx.x; r < C; r += NT) vj[r] = (float)((double)vj[r] * inv);
+        __syncthreads();
+        for (int k = j + 1 + warp; k < C; k += NW) {
+            float* vk = V + (size_t)k * ldv;
+            double dp = 0.0;
+            for (int r = lane; r < C; r += 32) dp += (double)vj[r] * (double)vk[r];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, off);
+            for (int r = lane; r < C; r += 32) vk[r] = (float)((double)vk[r] - dp * (double)vj[r]);
+        }
+        __syncthreads();
+    }
 }
 
 // V = I (Cp x Cp, stride ldv).

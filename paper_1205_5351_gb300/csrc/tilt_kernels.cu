@@ -147,14 +147,62 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
         V = a.Vg;
         stage = reinterpret_cast<unsigned char*>(L.svd);
     }
-    for (int e = threadIdx.x; e < d.ldb * d.Cp; e += NT) {
-        const int r = e % d.ldb, c = e / d.ldb;
-        B[e] = (r < d.R && c < d.C) ? a.M[(size_t)c * d.R + r] : 0.f;
+    int reorth = 0;
+    if (!a.Vio) {
+        for (int e = threadIdx.x; e < d.ldb * d.Cp; e += NT) {
+            const int r = e % d.ldb, c = e / d.ldb;
+            B[e] = (r < d.R && c < d.C) ? a.M[(size_t)c * d.R + r] : 0.f;
+        }
+        __syncthreads();
+        set_identity(V, d.ldv, d.Cp);
+    } else {
+        // warm start from the caller's V (padding: identity), re-orthonormalised in FP64 when it
+        // has drifted, then B = M V with the solver's product
+        for (int e = threadIdx.x; e < d.ldv * d.Cp; e += NT) {
+            const int r = e % d.ldv, c = e / d.ldv;
+            V[e] = (r < d.C && c < d.C) ? a.Vio[(size_t)c * d.C + r] : (r == c ? 1.f : 0.f);
+        }
+        __syncthreads();
+        if (v_drift(V, d.ldv, d.C, L.sc) > 1e-4f) {
+            v_reorth_fp64(V, d.ldv, d.C, L.sc);
+            reorth = 1;
+        }
+        for (int e = threadIdx.x; e < d.ldb * d.Cp; e += NT) B[e] = 0.f;
+        __syncthreads();
+        const float* Mx = a.M;
+        const int R = d.R, ldv = d.ldv, ldb = d.ldb;
+        auto la = [=](int r, int j) { return Mx[(size_t)j * R + r]; };
+        auto lb = [=](int j, int c) { return V[(size_t)c * ldv + j]; };
+        auto ep = [=](int r, int c, float v) { B[(size_t)c * ldb + r] = v; };
+        if (use_tc_products(d)) {
+            if (!tc_gemm<NT, false, true>(d.R, d.C, d.C, la, lb, ep, stage, TC_KC, 1, &L.sc->tc)) {
+                if (threadIdx.x == 0) a.out->status = -5;
+                tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+                return;
+            }
+        } else {
+            for (int e = threadIdx.x; e < d.R * d.C; e += NT) {
+                const int r = e % d.R, c = e / d.R;
+                float acc = 0.f;
+                for (int j = 0; j < d.C; ++j) acc = fmaf(la(r, j), lb(j, c), acc);
+                ep(r, c, acc);
+            }
+            __syncthreads();
+        }
     }
-    __syncthreads();
-    set_identity(V, d.ldv, d.Cp);
-    const int sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag,
-                                default_group_width(d.R, d.C), 0);
+    int sw;
+    if (jsched_order(a.jsched) == 2) {
+        sw = k2_jacobi_staged<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag, jsched_width(a.jsched),
+                                 reinterpret_cast<float*>(stage), &L.sc->tc);
+    } else {
+        sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag, jsched_width(a.jsched),
+                          jsched_order(a.jsched));
+    }
+    if (sw < 0) {
+        if (threadIdx.x == 0) a.out->status = -5;
+        tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+        return;
+    }
     svt_weights(B, d.ldb, d.R, d.C, a.eps, L.sigma, L.w, L.kept, L.sc);
     const int nk = L.sc->iscal[1];
     // the solver's SVT: coefficients Z = diag(w / sigma^2) B_K^T M and A = B_K Z, on the tensor
@@ -186,8 +234,11 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
         for (int e = threadIdx.x; e < d.S; e += NT) A[e] = 0.f;
     }
     for (int k = threadIdx.x; k < d.C; k += NT) a.sigma[k] = L.sigma[k];
+    if (a.Vio)
+        for (int e = threadIdx.x; e < d.C * d.C; e += NT) a.Vio[e] = V[(size_t)(e / d.C) * d.ldv + e % d.C];
     if (threadIdx.x == 0) {
         a.out->sweeps = sw;
+        a.out->reorth = reorth;
         a.out->status = ok ? 0 : -5;
     }
     tc_teardown(&L.sc->tc, TC_TMEM_COLS);
@@ -233,7 +284,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
     InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
-                             default_group_width(d.R, d.C), nullptr);
+                             a.jsched, nullptr);
     if (threadIdx.x == 0) {
         a.out->status = io.tc_timeout ? -5 : io.bad ? -1 : 0;
         a.out->iters = io.iters;
@@ -281,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1) adm_step_kernel(AdmArgs a) {
     double mu0 = a.mu0;
     if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(a.D, d, L.sigma, L.w, L.sc);
     const AdmOut o = k_inner_adm<4, true>(d, a.lam, a.tol, a.rho, mu0, a.max_iter, a.D, a.J, a.A, a.E, a.Y, buf, L,
-                                          default_schedule(d.R, d.C));
+                                          a.jsched);
     if (threadIdx.x == 0) {
         a.out->status = o.tc_timeout ? -5 : o.bad ? -1 : (o.converged ? 0 : 2);
         a.out->iters = o.iters;

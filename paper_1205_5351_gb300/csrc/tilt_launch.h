@@ -14,6 +14,7 @@ struct StepOut {
     int sweeps;           // svt / inner
     int iters;            // inner
     int status;           // 0 ok, -2 singular G
+    int reorth;           // svt: the warm start's V was re-orthonormalised in FP64
     double c1, c2, mu;    // inner
     double Q[3 * PMAX], G[PMAX * PMAX], Gi[PMAX * PMAX];
     double dtau[PMAX];
@@ -46,8 +47,11 @@ struct SvtArgs {
     float* Bg;    // global SVD buffers when !smem_svd
     float* Vg;
     float* Tg;
-    float* Zg;    // device, C * C floats
+    float* Zg;    // device, C * Cp floats
     float* sigma; // device, C floats
+    int jsched;   // Jacobi schedule (staged sweeps when the SVD buffers are in device memory)
+    float* Vio;   // nullptr: cold start; else C x C right singular vectors (stride C) to warm-start
+                  // from, overwritten with the new ones
     StepOut* out;
 };
 
@@ -65,6 +69,7 @@ struct InnerArgs {
     float* Zg;     // scratch C * C
     int m, n, ttype, smem_svd;
     int use_q;     // 0: no constraint rows (G = J^T J, W^T W = J_perp)
+    int jsched;    // Jacobi schedule
     double tau[PMAX];
     Params prm;
     double mu0;
@@ -81,7 +86,7 @@ struct AdmArgs {
     float* Vg;
     float* Tg;
     float* Zg;         // scratch C * Cp
-    int m, n, p, smem_svd, max_iter;
+    int m, n, p, smem_svd, max_iter, jsched;
     double lam, tol, rho, mu0;
     StepOut* out;
 };

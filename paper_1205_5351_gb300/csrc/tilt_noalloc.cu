@@ -72,6 +72,7 @@ extern "C" int tilt_svt_noalloc(const float* M_dev, int m, int n, float eps, flo
     a.n = n;
     a.eps = eps;
     a.smem_svd = (svd + head <= g_max_smem[dev]) ? 1 : 0;
+    a.jsched = default_group_width(d.R, d.C);
     a.Bg = s + OFF_B;
     a.Vg = s + OFF_V;
     a.Tg = nullptr;   // the SVT step keeps M in place of T

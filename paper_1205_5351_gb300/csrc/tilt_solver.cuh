@@ -13,7 +13,7 @@ enum { FS_IMU = 0, FS_THR = 1, FS_MU = 2, FS_IMUN = 3, FS_CC = 8 };
 enum { LOOP_GO = 0, LOOP_CONVERGED = 1, LOOP_BAD = 2, LOOP_CANCELLED = 3 };
 
 struct InnerOut {
-    int iters, sweeps, warm, rank;
+    int iters, sweeps, warm, reorth, rank;
     bool converged, bad, cancelled, tc_timeout;
     double c1, c2, mu_last, nuc, l1;
 };
@@ -38,7 +38,7 @@ __device__ inline float soft(float x, float eps) {
 
 struct SvtStepOut {
     int sweeps;
-    bool warm, tc_timeout;
+    bool warm, tc_timeout, reorth;
     unsigned long long t_svd_end;   // clock at the end of the SVD (start of the reconstruction)
 };
 
@@ -55,8 +55,14 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
     so.sweeps = 0;
     so.warm = false;
     so.tc_timeout = false;
-    bool warm = haveV && gate_ok;
-    if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) warm = false;   // re-orthogonalise by restarting
+    so.reorth = false;
+    const bool warm = haveV && gate_ok;
+    // FP32 rotations let V drift from orthogonal over many warm starts; past 1e-4 in a column
+    // norm it is re-orthonormalised in FP64 and the warm start goes ahead
+    if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) {
+        v_reorth_fp64(buf.V, ldv, C, sc);
+        so.reorth = true;
+    }
     if (warm) {
         if (TCP && buf.tc) {
             if (!warm_start_tc(buf.T, ldb, buf.V, ldv, buf.B, C, buf.stage, buf.nbuf, &sc->tc)) {
@@ -72,8 +78,19 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
         set_identity(buf.V, ldv, Cp);
     }
     so.warm = warm;
-    so.sweeps = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
-                               jsched_width(jsched), jsched_order(jsched));
+    if (TCP && jsched_order(jsched) == 2) {
+        so.sweeps = k2_jacobi_staged<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
+                                          jsched_width(jsched), reinterpret_cast<float*>(buf.stage), &sc->tc);
+        if (so.sweeps < 0) {
+            so.sweeps = 0;
+            so.tc_timeout = true;
+            so.t_svd_end = clk();
+            return so;
+        }
+    } else {
+        so.sweeps = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
+                                   jsched_width(jsched), jsched_order(jsched));
+    }
     haveV = true;
     svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
     so.t_svd_end = clk();
@@ -165,9 +182,9 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
                             bool& haveV, const SmemLayout& L, Result* cyc, int jsched, const int* cancel) {
     Scratch* sc = L.sc;
-    const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
+    const int p = d.p, S = d.S, R = d.R, ldb = d.ldb;
     InnerOut out;
-    out.iters = 0; out.sweeps = 0; out.warm = 0; out.rank = 0;
+    out.iters = 0; out.sweeps = 0; out.warm = 0; out.reorth = 0; out.rank = 0;
     out.cancelled = false;
     out.converged = false; out.bad = false; out.tc_timeout = false;
     out.c1 = out.c2 = 0.0; out.mu_last = mu0; out.nuc = 0.0; out.l1 = 0.0;
@@ -261,6 +278,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         const unsigned long long t1 = so.t_svd_end;
         if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
         if (so.warm) out.warm++;
+        if (so.reorth) out.reorth++;
         out.sweeps += so.sweeps;
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
@@ -604,7 +622,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
 
     int status = sc->iscal[7] ? -4 : 1;
     bool inner_maxed = false;
-    int outer = 0, inner_total = 0, sweeps = 0, warm = 0, rank = 0;
+    int outer = 0, inner_total = 0, sweeps = 0, warm = 0, reorth = 0, rank = 0;
     double c1 = 0.0, nuc = 0.0, l1 = 0.0;
     bool haveV = false;
 
@@ -643,6 +661,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             inner_total += io.iters;
             sweeps += io.sweeps;
             warm += io.warm;
+            reorth += io.reorth;
             c1 = io.c1; nuc = io.nuc; l1 = io.l1; rank = io.rank;
             if (io.tc_timeout) { status = -5; break; }
             if (io.bad) { status = -1; break; }
@@ -680,6 +699,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
         res.inner_iters = inner_total;
         res.svd_sweeps = sweeps;
         res.svd_warm = warm;
+        res.svd_reorth = reorth;
         res.oob_pixels = sc->iscal[0];
         res.kkt_residual = c1;
     }

@@ -21,10 +21,12 @@ constexpr int TC_M = 128;          // rows of one accumulator tile (tensor-memor
 constexpr int TC_NMAX = 256;       // columns of the accumulator (tensor-memory columns)
 constexpr long long TC_WAIT_LIMIT = 1ll << 22;   // polls of an mbarrier before giving up
 
-// Per-CTA state of the tensor-core path (in shared memory).
+// Per-CTA state of the tensor-core path and of the bulk copies (in shared memory).
 struct TcState {
     uint64_t mbar[2];      // one mbarrier per stage buffer
+    uint64_t jbar;         // completion of the bulk copies of the staged Jacobi sweeps
     uint32_t phase[2];     // parity each mbarrier waits for next
+    uint32_t jphase;
     uint32_t tmem;         // tensor-memory base address of the accumulator
     int error;             // non-zero once a bounded wait gave up
 };
@@ -69,6 +71,36 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
     return false;
 }
+
+// ---- bulk copies (the TMA engine's one-dimensional copies), issued by one thread.  Both
+// addresses 16-byte aligned, sizes multiples of 16 bytes.
+// Arrive on the mbarrier and make its current phase also wait for `bytes` of transfers.
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared; completion is counted on the mbarrier
+__device__ inline void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst_smem)),
+                 "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// shared -> global, in the issuing thread's current bulk group
+__device__ inline void bulk_s2g(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem), "r"(smem_u32(src_smem)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the issuing thread's bulk groups, all but the `n` most recent, have finished reading shared memory
+template <int N>
+__device__ inline void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+// the issuing thread's bulk groups have completed (their writes are performed)
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's generic-proxy memory accesses before later async-proxy (bulk copy,
+// tensor core) accesses, and async-proxy writes already waited for before later generic ones
+__device__ inline void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading-dimension byte offset
 // (between core matrices adjacent along K), stride-dimension byte offset (between 8-row
@@ -166,7 +198,9 @@ __device__ inline void tc_setup(TcState* st, uint32_t ncols) {
     if (threadIdx.x == 0) {
         mbar_init(&st->mbar[0], 1);
         mbar_init(&st->mbar[1], 1);
+        mbar_init(&st->jbar, 1);
         st->phase[0] = st->phase[1] = 0;
+        st->jphase = 0;
         st->error = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }

@@ -50,7 +50,7 @@ class Result(ctypes.Structure):
                 ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("svd_sweeps", ctypes.c_int),
                 ("svd_warm", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("kkt_residual", ctypes.c_double),
                 ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5),
-                ("launch_class", ctypes.c_int)]
+                ("launch_class", ctypes.c_int), ("svd_reorth", ctypes.c_int)]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Result":
@@ -65,7 +65,8 @@ class Result(ctypes.Structure):
                     lam=self.lambda_, rank=self.rank_A, outer_iters=self.outer_iters,
                     inner_iters=self.inner_iters, svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm,
                     oob=self.oob_pixels, kkt=self.kkt_residual, latency_ms=self.latency_ms,
-                    phase_cycles=list(self.phase_cycles), launch_class=self.launch_class)
+                    phase_cycles=list(self.phase_cycles), launch_class=self.launch_class,
+                    svd_reorth=self.svd_reorth)
 
 
 class Problem(ctypes.Structure):
@@ -97,6 +98,7 @@ SIGNATURES = {
     "tilt_inner": (_i, [_vp, _vp, _vp, _i, _i, _P(_d), _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d),
                         _P(_d), _P(_d), _P(_d)]),
     "tilt_svt_noalloc": (_i, [_vp, _i, _i, ctypes.c_float, _vp, _vp, _vp]),
+    "tilt_svt_warm": (_i, [_vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _P(ctypes.c_float), _P(_i), _P(_i)]),
     "tilt_inner_adm": (_i, [_vp, _vp, _vp, _i, _i, _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d), _P(_d),
                             _P(_i)]),
     "tilt_best_of": (_i, [_P(Result), _i, _i, _P(_i)]),
@@ -332,6 +334,18 @@ class Context:
         sw = ctypes.c_int()
         _check(lib().tilt_svt(self.h, _dptr(M_t), m, n, float(eps), _dptr(A), sig, ctypes.byref(sw)), self.h)
         return A, np.array(sig, dtype=np.float32), sw.value
+
+    def svt_warm(self, M_t, m: int, n: int, eps: float, V_t):
+        """tilt_svt_warm: V_t (CUDA, C x C column-major, C = min(m, n)) is the warm start and
+        receives the new right singular vectors; returns (A, sigma, sweeps, reorth)."""
+        import torch
+        A = torch.empty(m * n, dtype=torch.float32, device=M_t.device)
+        C = min(m, n)
+        sig = (ctypes.c_float * C)()
+        sw, ro = ctypes.c_int(), ctypes.c_int()
+        _check(lib().tilt_svt_warm(self.h, _dptr(M_t), m, n, float(eps), _dptr(V_t), _dptr(A), sig, ctypes.byref(sw),
+                                   ctypes.byref(ro)), self.h)
+        return A, np.array(sig, dtype=np.float32), sw.value, ro.value
 
     def inner_adm(self, D_t, J_t, m: int, n: int, p: int, params: Params | None, mu0: float = -1.0) -> dict:
         """The ADM baseline (tilt_inner_adm); returns A, E, Y (flat CUDA tensors, long layout),

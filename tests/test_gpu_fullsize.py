@@ -40,6 +40,9 @@ def _properties(T, patches, res, eps1):
         # the constraint Q dtau = 0 keeps the window centre (affine: exactly the translation)
         if p.ttype == 6:
             assert abs(r["tau"][2] - p.tau0[2]) < 1e-6 and abs(r["tau"][5] - p.tau0[5]) < 1e-6
+        # every SVD after the first of a solve is warm-started: a V that drifted from
+        # orthogonal is re-orthonormalised in FP64 instead of restarting cold
+        assert r["svd_warm"] == r["inner_iters"] - 1, (r["svd_warm"], r["inner_iters"])
 
 
 def test_affine_batch_1024_full_size(T):

@@ -202,3 +202,31 @@ def test_end_to_end_mixed_batch_sample(T, ctx, first):
         ref = O.tilt(p.img.astype(np.float64), p.tau0, p.ttype, p.m, p.n, O.Params())
         assert O.tau_error(r["tau"], ref.tau) <= 1e-3, (p.m, p.n, r["tau"], ref.tau)
         assert r["rank"] == ref.rank
+
+
+@pytest.mark.parametrize("seed,m,n", [(61, 64, 50), (62, 200, 160)])
+def test_warm_svt_reorthonormalises_a_drifted_v(T, ctx, seed, m, n):
+    # the solver's warm start (Sec. 5) from the right singular vectors of a nearby matrix: an
+    # orthonormal V is used as it is; a V whose column norms drifted past 1e-4 is first
+    # re-orthonormalised in FP64; either way the SVT matches the oracle's and V comes back
+    # orthonormal.  (200 x 160 runs the warm-start product on the tensor cores.)
+    rng = np.random.default_rng(seed)
+    r = max(2, n // 8)
+    M0 = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) / math.sqrt(n) + 0.02 * rng.standard_normal((m, n))
+    M = (M0 + 0.01 * rng.standard_normal((m, n))).astype(np.float32)
+    V0 = np.linalg.svd(M0)[2].T                      # n x n (m >= n: X = M)
+    s = np.linalg.svd(M.astype(np.float64), compute_uv=False)
+    eps = float(s[r] * 1.5)
+    Aref = O.svt(M.astype(np.float64), eps)[0]
+    M_t = torch.from_numpy(T.to_long_layout(M)).cuda()
+    _, _, cold_sweeps = ctx.svt(M_t, m, n, eps)
+    for drift, want_reorth in ((0.0, 0), (3e-3, 1)):
+        V = V0 @ (np.eye(n) + drift * rng.standard_normal((n, n)))
+        V_t = torch.from_numpy(np.ascontiguousarray(V.T).astype(np.float32).reshape(-1)).cuda()   # column-major
+        A_d, sig, sweeps, reorth = ctx.svt_warm(M_t, m, n, eps, V_t)
+        assert reorth == want_reorth
+        assert rel(T.from_long_layout(A_d.cpu().numpy(), m, n), Aref) <= 1e-5
+        assert rel(np.sort(sig)[::-1], s) <= 1e-5
+        Vn = V_t.cpu().numpy().reshape(n, n).T.astype(np.float64)
+        assert np.abs(Vn.T @ Vn - np.eye(n)).max() <= 1e-5
+        assert sweeps < cold_sweeps
