@@ -127,9 +127,13 @@ def parse_args():
     ap.add_argument("--parity-patches", type=int, default=64, help="size of the stratified parity sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stream-seconds", type=float, default=600.0, help="wall-clock cap of the served stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="arrival rate of the served stream (patches/s)")
     ap.add_argument("--no-autotune", action="store_true", help="skip autotuning (profiling captures)")
     ap.add_argument("--max-outer", type=int, default=None, help="override (small profiling cases only)")
     ap.add_argument("--max-inner", type=int, default=None, help="override (small profiling cases only)")
+    ap.add_argument("--svd-ws", choices=["jacobi", "cayley"], default="jacobi",
+                    help="SVD warm start: warm-started Jacobi (default) or the paper's Algorithm 2")
+    ap.add_argument("--eps-svd", type=float, default=0.05, help="gate of Algorithm 2 (with --svd-ws cayley)")
     return ap.parse_args()
 
 
@@ -137,10 +141,10 @@ def parse_args():
 def _oracle_one(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import tilt_oracle as O
-    idx, first, workload = args
+    idx, first, workload, extra = args
     p = make_patches(workload, 1, first + idx)[0]
     t0 = time.perf_counter()
-    r = O.tilt(p.img.astype("float64"), p.tau0, p.ttype, p.m, p.n, O.Params(**WORKLOADS[workload][2]))
+    r = O.tilt(p.img.astype("float64"), p.tau0, p.ttype, p.m, p.n, O.Params(**{**WORKLOADS[workload][2], **extra}))
     return idx, time.perf_counter() - t0, r.tau.tolist(), r.inner_iters, r.rank
 
 
@@ -153,7 +157,7 @@ def cpu_pool():
     return mp.get_context("spawn").Pool(cores), cores
 
 
-def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload="affine", indices=None):
+def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload="affine", indices=None, extra=None):
     """Oracle on patches first, first+1, ... (or on the given indices, in that order) until about
     budget_s of wall time is spent, ``cores`` patches at a time."""
     order = list(indices) if indices is not None else list(range(max_patches or 4 * cores))
@@ -162,7 +166,7 @@ def run_oracle_sample(pool, cores, budget_s, first=0, max_patches=None, workload
     nxt = 0
     while nxt < len(order) and (time.perf_counter() - t0) < budget_s:
         batch = order[nxt:nxt + cores]
-        out += pool.map(_oracle_one, [(i, first, workload) for i in batch])
+        out += pool.map(_oracle_one, [(i, first, workload, extra or {}) for i in batch])
         nxt += len(batch)
     wall = time.perf_counter() - t0
     return out, wall
@@ -310,6 +314,8 @@ def run_ours(args, rank, world, local_rank, dist):
     flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)
     ctx = tilt.Context(local_rank)
     over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
+    if args.svd_ws == "cayley":
+        over = {**over, "svd_ws": 1, "eps_svd": args.eps_svd}
     params = tilt.default_params(**{**wl_params, **over})
 
     def step(items, on_device, planes):
@@ -442,7 +448,9 @@ def run_ours(args, rank, world, local_rank, dist):
             "kcycles_per_inner_iter": round(sum(sum(r["phase_cycles"]) for r in results) / max(1, inner) / 1e3, 2),
             "svd": {"sweeps_per_svd": sum(r["svd_sweeps"] for r in results) / max(1, inner),
                     "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner),
-                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results)},
+                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results),
+                    "warm_start": args.svd_ws,
+                    "cayley_steps_fraction": sum(r["svd_cayley"] for r in results) / max(1, inner)},
             "phase_split": dict(zip(["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"],
                                     [round(sum(r["phase_cycles"][i] for r in results) /
                                            max(1, sum(sum(r["phase_cycles"]) for r in results)), 4)
@@ -505,8 +513,9 @@ def run_ours(args, rank, world, local_rank, dist):
             out["speedup_vs_plain_gpu"] = value / plain if plain > 0 else None
         if pool is not None:
             idx_s = stratified_sample(patches, results, lat, args.parity_patches)
+            extra = {"svd_warm": True, "eps_svd": args.eps_svd} if args.svd_ws == "cayley" else {}
             sample, wall = run_oracle_sample(pool, cores, args.cpu_seconds, first=first, workload=args.workload,
-                                             indices=idx_s)
+                                             indices=idx_s, extra=extra)
             pool.close()
             errs, rank_eq = [], 0
             for idx, secs, tau, iters, rk in sample:
@@ -535,7 +544,7 @@ def run_ours(args, rank, world, local_rank, dist):
 
 # ----------------------------------------------------------------------------- served stream
 def run_stream(args, rank, world, local_rank):
-    """Poisson arrivals (2000/s) of patches with sides 32..256, half affine / half projective,
+    """Poisson arrivals (--rate, 2000/s by default) of patches with sides 32..256, half affine / half projective,
     submitted one by one from host memory as they arrive and polled to completion; reports
     throughput and submit-to-completion latency percentiles."""
     import torch
@@ -544,7 +553,7 @@ def run_stream(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     n = args.patches or 2000
-    times, patches = synth.served_stream(n, first=rank * n)
+    times, patches = synth.served_stream(n, rate_hz=args.rate, first=rank * n)
     over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
     params = tilt.default_params(**over)
     ctx = tilt.Context(local_rank)
@@ -587,9 +596,9 @@ def run_stream(args, rank, world, local_rank):
     return {"metric": METRIC, "value": len(lat) / wall, "unit": "patches/s", "n_gpus": world, "steps": 1,
             "warmup": len(warm), "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "served stream: Poisson arrivals at 2000/s, sides uniform 32-256, half affine / "
-                                   "half projective, rank 1-6, corruption 0-15 %", "arrivals": n,
-                       "offered_rate_per_s": 2000.0},
+            "config": {"workload": "served stream: Poisson arrivals at %g/s, sides uniform 32-256, half affine / "
+                                   "half projective, rank 1-6, corruption 0-15 %%" % args.rate, "arrivals": n,
+                       "offered_rate_per_s": args.rate},
             "completed": len(lat), "submitted": submitted, "ladmap_iters_per_s": inner / wall,
             "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
                            "note": "arrival time to completion (queueing included)"},

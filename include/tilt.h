@@ -87,6 +87,14 @@ typedef struct {
     int max_outer;     /* outer steps (default 10)                                            */
     double outer_tol;  /* stop when dtau moves no window corner by more than this many
                           pixels (default 1e-2)                                               */
+    int svd_ws;        /* SVD warm start: 0 (default) the previous right singular vectors feed
+                          one-sided Jacobi sweeps, which end at an exact SVD; 1 the paper's
+                          Algorithm 2: when ||M_k - M_k-1||_F < eps_svd ||M_k||_F (eps_svd < 0:
+                          always) take one step along the Cayley curve from the previous
+                          factors (tilt_svd_cayley) and threshold that approximate SVD, doing
+                          a full SVD when the step is refused; the first SVD of every inner
+                          loop is full.  Extra device memory per problem: about 8 R C + R^2
+                          floats                                                          */
 } tilt_params;
 
 /* Result of one problem. */
@@ -123,6 +131,7 @@ typedef struct {
     int svd_reorth;      /* warm starts whose right singular vectors had drifted from
                             orthogonal (a column norm off by more than 1e-4) and were
                             re-orthonormalised in FP64 first                                */
+    int svd_cayley;      /* SVDs taken from an accepted step of Algorithm 2 (svd_ws = 1)     */
 } tilt_result;
 
 /* Fill *p with the default parameters. */
@@ -239,6 +248,23 @@ int tilt_gram(tilt_ctx* ctx, const float* J_dev, int m, int n, const double* tau
 int tilt_svt(tilt_ctx* ctx, const float* M_dev, int m, int n, float eps, float* A_dev,
              float* sigma_out, int* sweeps_out);
 
+/* One step of the paper's SVD warm start, Algorithm 2 (Sec. 5, Appendix A): from the factors
+ * U (R x C, columns orthonormal), Sigma (C, signed) and V (C x C, orthogonal) of the previous
+ * matrix, compute the projected gradients P_U = X M^T - M X^T, P_V = X^T M - M^T X and
+ * P_Sigma = Sigma - diag(U^T M V) with X = U Sigma V^T, the derivatives f'(0), f''(0) of
+ * f(t) = 1/2 ||M - U(t) Sigma(t) V(t)^T||_F^2 along the Cayley curve of Eq. curve_to_search,
+ * t = -f'(0) / f''(0), and the curve point (U(t) = (I + t/2 P_U)^-1 (I - t/2 P_U) U, Sigma(t) =
+ * Sigma - t P_Sigma, V(t) likewise).  The step is accepted when f''(0) > 0 and f(t) <= f(0),
+ * and then U_dev, S_dev, V_dev are overwritten with the curve point; otherwise they are left
+ * as they were (the solver then computes a full SVD).  M_dev: the m x n matrix in the
+ * long-side layout above, as the R x C matrix X (R = max(m, n), C = min(m, n)); U_dev R x C
+ * column-major (stride R), S_dev C, V_dev C x C column-major (stride C), all device memory.
+ * Outputs (host, may be NULL): f'(0), f''(0), t and whether the step was accepted.  FP32
+ * products on the SIMT pipes, the two (R x R and C x C) linear systems by Gauss-Jordan
+ * elimination with partial pivoting.  Errors: TILT_E_INVAL, TILT_E_CUDA. */
+int tilt_svd_cayley(tilt_ctx* ctx, const float* M_dev, int m, int n, float* U_dev, float* S_dev, float* V_dev,
+                    double* f1_out, double* f2_out, double* t_out, int* accepted_out);
+
 /* tilt_svt warm-started as the solver warm-starts every SVD after the first (Sec. 5): from the
  * right singular vectors V of the previous iteration's M, re-orthonormalised first in FP64
  * (modified Gram-Schmidt) when a column norm of V is off by more than 1e-4 (FP32 rotations
@@ -279,6 +305,12 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
 int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m, int n, int p,
                    const tilt_params* params, double mu0, float* A_dev, float* E_dev, float* Y_dev,
                    int* iters_out, double* dtau_out, double* residual_out, int* sweeps_out);
+
+/* Counters of the most recent step entry point on this context (tilt_svt, tilt_svt_warm,
+ * tilt_inner, tilt_inner_adm): Jacobi sweeps and, for tilt_inner with svd_ws = 1, the
+ * iterations whose SVD came from an accepted step of Algorithm 2.  Either pointer may be NULL.
+ * Errors: TILT_E_INVAL. */
+int tilt_step_counters(tilt_ctx* ctx, int* sweeps_out, int* cayley_steps_out);
 
 /* ------------------------------------------------------------------------------------------
  * Allocation-free singular value thresholding.  (The paper has no counterpart: this is a

@@ -93,7 +93,8 @@ private:
 };
 
 struct Layout {   // byte offsets inside one problem's workspace
-    size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, order, total;
+    size_t dhat, j, a, e, y, p, mp, zg, bg, vg, tg, img, cay, order, total;
+    bool has_cay;
     int smem_svd, minb, jsched, tc_nbuf;
     size_t smem;
 };
@@ -181,6 +182,7 @@ struct tilt_ctx {
     std::map<std::pair<int, int>, int> tune;
     int force_js = 0;               // non-zero while the autotuner times a candidate schedule
     std::string tune_path;
+    int last_cayley = 0;            // accepted Algorithm-2 steps of the last tilt_inner call
 };
 
 namespace {
@@ -200,12 +202,13 @@ Params to_params(const tilt_params* p) {
     q.outer_tol = p->outer_tol;
     q.max_inner = p->max_inner;
     q.max_outer = p->max_outer;
+    q.svd_ws = p->svd_ws;
     return q;
 }
 
 bool params_ok(const Params& q) {
     return q.eps1 >= 0 && q.eps2 >= 0 && q.rho0 >= 1.0 && q.mu_max > 0 && q.max_inner >= 1 && q.max_outer >= 1 &&
-           q.outer_tol >= 0 && std::isfinite(q.lam) && std::isfinite(q.mu0);
+           q.outer_tol >= 0 && std::isfinite(q.lam) && std::isfinite(q.mu0) && (q.svd_ws == 0 || q.svd_ws == 1);
 }
 
 std::pair<int, int> size_bucket(int R, int C) { return {(R + 15) / 16, (C + 15) / 16}; }
@@ -223,7 +226,7 @@ bool jsched_valid(int js) {
     return (w == 4 || w == 8 || w == 16) && (o == 0 || o == 1);
 }
 
-Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_img) {
+Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_img, bool cayley) {
     Layout L{};
     const Dims d = make_dims(m, n, p);
     const size_t S = (size_t)d.S * sizeof(float);
@@ -289,6 +292,8 @@ Layout plan(const tilt_ctx* ctx, int m, int n, int p, int H, int W, bool copy_im
         }
     }
     L.img = copy_img ? take((size_t)H * W * sizeof(float)) : 0;
+    L.cay = cayley ? take(cayley_floats(d) * sizeof(float)) : 0;
+    L.has_cay = cayley;
     L.order = take(sizeof(int));
     L.total = o;
     return L;
@@ -342,6 +347,7 @@ int prepare(tilt_ctx* ctx, Ticket& t, cudaStream_t st) {
     pr.pl.Bg = (L.smem_svd & 1) ? nullptr : reinterpret_cast<float*>(base + L.bg);
     pr.pl.Vg = (L.smem_svd & 2) ? nullptr : reinterpret_cast<float*>(base + L.vg);
     pr.pl.Tg = (L.smem_svd & 4) ? nullptr : reinterpret_cast<float*>(base + L.tg);
+    pr.pl.Cay = L.has_cay ? reinterpret_cast<float*>(base + L.cay) : nullptr;
     pr.smem_svd = L.smem_svd;
     pr.tc_nbuf = L.tc_nbuf;
     pr.jsched = L.jsched;
@@ -463,7 +469,7 @@ int admit_waiting(tilt_ctx* ctx) {
 // with the tensor-core products (short side >= TC_MIN_C) or with no SVD buffer in shared
 // memory.
 int launch_class_of(const Layout& L) {
-    if (L.tc_nbuf > 0 || !L.smem_svd) return 2;
+    if (L.tc_nbuf > 0 || !L.smem_svd || L.has_cay) return 2;
     return L.minb == 2 ? 0 : 1;
 }
 
@@ -489,6 +495,7 @@ void fill_result(const Result& r, const Ticket& t, tilt_result* out) {
     out->phase_cycles[4] = r.cyc_other;
     out->launch_class = t.batch < 0 ? -1 : t.klass;
     out->svd_reorth = r.svd_reorth;
+    out->svd_cayley = r.svd_cayley;
 }
 
 // Copy the device planes A and E (long-side-contiguous) to host m x n row-major arrays (either
@@ -575,6 +582,7 @@ void tilt_default_params(tilt_params* p) {
     p->max_inner = 500;
     p->max_outer = 10;
     p->outer_tol = 1e-2;
+    p->svd_ws = 0;
 }
 
 const char* tilt_last_error(tilt_ctx*) { return g_err.c_str(); }
@@ -664,7 +672,7 @@ int tilt_submit(tilt_ctx* ctx, const float* img, int H, int W, size_t ld_elems, 
         if (!std::isfinite(tau0[k])) return fail(TILT_E_INVAL, "non-finite tau0");
     t.req.prm = to_params(params);
     if (!params_ok(t.req.prm)) return fail(TILT_E_INVAL, "parameters out of range");
-    t.lay = plan(ctx, m, n, (int)type, H, W, !is_device_ptr);
+    t.lay = plan(ctx, m, n, (int)type, H, W, !is_device_ptr, t.req.prm.svd_ws == 1);
     t.ws_bytes = t.lay.total;
     if (t.ws_bytes > ctx->pool.size())
         return fail(TILT_E_NOMEM, "problem needs %zu bytes, budget is %zu", t.ws_bytes, ctx->pool.size());
@@ -720,7 +728,7 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         t.req.p = pb.type;
         for (int k = 0; k < 8; ++k) t.req.tau0[k] = k < pb.type ? pb.tau0[k] : 0.0;
         t.req.prm = prm;
-        t.lay = plan(ctx, pb.m, pb.n, pb.type, pb.H, pb.W, !is_device_ptr);
+        t.lay = plan(ctx, pb.m, pb.n, pb.type, pb.H, pb.W, !is_device_ptr, prm.svd_ws == 1);
         t.ws_bytes = t.lay.total;
         t.m = pb.m;
         t.n = pb.n;
@@ -1146,15 +1154,17 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     step_plan(ctx, d, svd, head, &a.smem_svd, &a.jsched, &smem);
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
-    const size_t need = sizeof(float) * (2 * S4 + nz + (a.smem_svd ? 0 : (2 * nb + nv)));
+    const size_t ncay = a.prm.svd_ws == 1 ? ((cayley_floats(d) + 63) & ~(size_t)63) : 0;
+    const size_t need = sizeof(float) * (2 * S4 + nz + ncay + (a.smem_svd ? 0 : (2 * nb + nv)));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
     float* s = reinterpret_cast<float*>(ctx->scratch);
     a.P = s;
     a.Mp = s + S4;
     a.Zg = a.Mp + S4;
+    a.Cay = ncay ? a.Zg + nz : nullptr;
     if (!a.smem_svd) {
-        a.Bg = a.Zg + nz;
+        a.Bg = a.Zg + nz + ncay;
         a.Vg = a.Bg + nb;
         a.Tg = a.Vg + nv;
     }
@@ -1177,9 +1187,45 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     if (iters_out) *iters_out = o.iters;
     if (dtau_out)
         for (int k = 0; k < (int)type; ++k) dtau_out[k] = o.dtau[k];
+    ctx->last_cayley = o.accepted;
     if (c1_out) *c1_out = o.c1;
     if (c2_out) *c2_out = o.c2;
     if (mu_out) *mu_out = o.mu;
+    return TILT_OK;
+}
+
+int tilt_step_counters(tilt_ctx* ctx, int* sweeps_out, int* cayley_steps_out) {
+    if (!ctx) return fail(TILT_E_INVAL, "null context");
+    if (sweeps_out) *sweeps_out = ctx->step_out->sweeps;
+    if (cayley_steps_out) *cayley_steps_out = ctx->last_cayley;
+    return TILT_OK;
+}
+
+int tilt_svd_cayley(tilt_ctx* ctx, const float* M_dev, int m, int n, float* U_dev, float* S_dev, float* V_dev,
+                    double* f1_out, double* f2_out, double* t_out, int* accepted_out) {
+    if (!ctx || !M_dev || !U_dev || !S_dev || !V_dev) return fail(TILT_E_INVAL, "null argument");
+    if (m < 1 || n < 1 || m > MAX_SIDE || n > MAX_SIDE) return fail(TILT_E_INVAL, "matrix %d x %d", m, n);
+    const Dims d = make_dims(m, n, 0);
+    const size_t need = sizeof(float) * (cayley_floats(d) + (size_t)d.ldb * d.Cp + (size_t)d.ldv * d.Cp);
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    CayArgs a{};
+    a.M = M_dev;
+    a.U = U_dev;
+    a.S = S_dev;
+    a.V = V_dev;
+    a.work = reinterpret_cast<float*>(ctx->scratch);
+    a.m = m;
+    a.n = n;
+    a.out = ctx->step_out_dev;
+    CUDA_TRY(launch_cayley_step(a, ctx->streams[0]));
+    rc = run_step(ctx);
+    if (rc) return rc;
+    const StepOut& o = *ctx->step_out;
+    if (f1_out) *f1_out = o.cay[0];
+    if (f2_out) *f2_out = o.cay[1];
+    if (t_out) *t_out = o.cay[2];
+    if (accepted_out) *accepted_out = o.accepted;
     return TILT_OK;
 }
 

@@ -25,6 +25,7 @@ constexpr int MAX_SIDE = 512;
 struct Params {
     double lam, eps1, eps2, rho0, mu0, mu_max, eps_svd, outer_tol;
     int max_inner, max_outer;
+    int svd_ws;            // 0: warm-started Jacobi; 1: Algorithm 2 (Cayley step) when the gate allows
 };
 
 // Per-problem result record (written once, at the end of the solve).
@@ -34,7 +35,7 @@ struct Result {
     double tau[8];
     double objective;
     double lambda;
-    int rank_A, outer_iters, inner_iters, svd_sweeps, svd_warm, svd_reorth, oob_pixels;
+    int rank_A, outer_iters, inner_iters, svd_sweeps, svd_warm, svd_reorth, svd_cayley, oob_pixels;
     double kkt_residual;
     // per-phase clock counters (SM cycles), for the time split of the fused solver
     unsigned long long cyc_warp, cyc_svd, cyc_recon, cyc_elem, cyc_other;
@@ -53,6 +54,7 @@ struct Planes {
     float* Vg;     // ldv * Cp
     float* Tg;     // ldb * Cp
     float* Zg;     // C * Cp   (X^T b_k of the kept columns, for the reconstruction; rows at stride Cp)
+    float* Cay;    // cayley_floats() (Algorithm 2 workspace; only when Params::svd_ws = 1)
 };
 
 // One problem as the solver kernel sees it.
@@ -1030,6 +1032,12 @@ constexpr int JSCHED_STAGED = 512;  // schedule: staged block pairs (width field
 __host__ __device__ inline int jsched_width(int js) { return js & 255; }
 __host__ __device__ inline int jsched_order(int js) { return js >> 8; }
 
+// Device-memory floats of the workspace of the SVD warm start of Algorithm 2 (tilt_cayley.cuh):
+// eight R x C planes, P_U (R x R), P_V and a C x C right-hand side, Sigma.
+__host__ __device__ inline size_t cayley_floats(const Dims& d) {
+    return (size_t)8 * d.ldb * d.Cp + (size_t)d.ldb * d.ldb + (size_t)2 * d.ldv * d.Cp + (size_t)d.Cp;
+}
+
 // Staged sweeps (matrices whose B and V live in device memory): shared-memory bytes of the
 // three column blocks of width b, and the widest even b <= 16 whose blocks fit in `avail`
 // bytes (0 when none does).
@@ -1050,24 +1058,11 @@ __host__ __device__ inline int default_schedule(int R, int C) {
     return ((R > 128 && C >= 64) ? 16 : 8) | JSCHED_BLOCK;
 }
 
-// Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the
-// list of kept columns.  Returns (via scal) sum (sigma - eps)_+, max (sigma - eps)_+ and
-// the kept count (iscal[1]).
-static __device__ void svt_weights(const float* B, int ldb, int R, int C, float eps, float* sigma, float* w, int* kept,
-                            Scratch* sc) {
+// The kept columns (w_k > 0) in ascending order, sum and max of (sigma_k - eps)_+ over them
+// and the numerical rank at 1e-3 of the largest (scal[3], scal[4], iscal[2]; the kept count in
+// iscal[1]).  All threads.
+static __device__ void svt_select(int C, float eps, const float* sigma, const float* w, int* kept, Scratch* sc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < C; k += NW) {
-        const float* bk = B + (size_t)k * ldb;
-        float s = 0.f;
-        for (int r = lane; r < R; r += 32) s = fmaf(bk[r], bk[r], s);
-        s = warp_sum(s);
-        if (lane == 0) {
-            const float sg = sqrtf(s);
-            sigma[k] = sg;
-            w[k] = (sg > eps) ? (sg - eps) / sg : 0.f;
-        }
-    }
-    __syncthreads();
     if (warp == 0) {
         // kept columns in ascending order (ballot and prefix count), sum and max of
         // (sigma - eps)_+ over them, then the numerical rank at 1e-3 of the largest
@@ -1103,6 +1098,27 @@ static __device__ void svt_weights(const float* B, int ldb, int R, int C, float 
         }
     }
     __syncthreads();
+}
+
+// Column norms sigma_k = ||b_k||, weights w_k = max(sigma_k - eps, 0) / sigma_k and the
+// list of kept columns.  Returns (via scal) sum (sigma - eps)_+, max (sigma - eps)_+ and
+// the kept count (iscal[1]).
+static __device__ void svt_weights(const float* B, int ldb, int R, int C, float eps, float* sigma, float* w, int* kept,
+                            Scratch* sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < C; k += NW) {
+        const float* bk = B + (size_t)k * ldb;
+        float s = 0.f;
+        for (int r = lane; r < R; r += 32) s = fmaf(bk[r], bk[r], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            const float sg = sqrtf(s);
+            sigma[k] = sg;
+            w[k] = (sg > eps) ? (sg - eps) / sg : 0.f;
+        }
+    }
+    __syncthreads();
+    svt_select(C, eps, sigma, w, kept, sc);
 }
 
 // Reconstruction coefficients of the singular value thresholding from the left factor:

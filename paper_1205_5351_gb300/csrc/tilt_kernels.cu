@@ -1,4 +1,5 @@
 // Kernels of the TILT-by-LADMAP solver for sm_103a and their host launchers.
+#include "tilt_cayley.cuh"
 #include "tilt_launch.h"
 #include "tilt_solver.cuh"
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
     InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
-                             a.jsched, nullptr);
+                             a.jsched, nullptr, a.Cay);
     if (threadIdx.x == 0) {
         a.out->status = io.tc_timeout ? -5 : io.bad ? -1 : 0;
         a.out->iters = io.iters;
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
         a.out->c1 = io.c1;
         a.out->c2 = io.c2;
         a.out->mu = io.mu_last;
+        a.out->accepted = io.cayley;
         for (int k = 0; k < PMAX; ++k) a.out->dtau[k] = k < a.ttype ? L.sc->cvec[k] : 0.0;
     }
     tc_teardown(&L.sc->tc, TC_TMEM_COLS);
@@ -342,6 +344,44 @@ __global__ void __launch_bounds__(NT, 1) adm_step_kernel(AdmArgs a) {
         for (int k = 0; k < PMAX; ++k) a.out->dtau[k] = k < a.p ? L.sc->dtau[k] : 0.0;
     }
     tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+}
+
+// One step of Algorithm 2 (the SVD warm start of Sec. 5) on given factors.  Workspace:
+// the Cayley buffers, then M and V at the strides the step uses (ldb, ldv).
+__global__ void __launch_bounds__(NT, 1) cayley_step_kernel(CayArgs a) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    SmemLayout L = carve_smem(smem_raw);
+    const Dims d = make_dims(a.m, a.n, 0);
+    const int R = d.R, C = d.C;
+    CayBufs cb = carve_cayley(a.work, d);
+    float* Mx = a.work + cayley_floats(d);
+    float* Vw = Mx + (size_t)d.ldb * d.Cp;
+    for (int e = threadIdx.x; e < d.ldb * C; e += NT) {
+        const int r = e % d.ldb, c = e / d.ldb;
+        Mx[e] = r < R ? a.M[(size_t)c * R + r] : 0.f;
+        cb.U[e] = r < R ? a.U[(size_t)c * R + r] : 0.f;
+    }
+    for (int e = threadIdx.x; e < d.ldv * C; e += NT) {
+        const int r = e % d.ldv, c = e / d.ldv;
+        Vw[e] = r < C ? a.V[(size_t)c * C + r] : 0.f;
+    }
+    for (int i = threadIdx.x; i < C; i += NT) cb.S[i] = a.S[i];
+    __syncthreads();
+    const CayleyOut o = cayley_step(d, Mx, cb, Vw, L.sc);
+    if (o.accepted) {
+        for (int e = threadIdx.x; e < R * C; e += NT) a.U[e] = cb.U[(size_t)(e / R) * d.ldb + e % R];
+        for (int e = threadIdx.x; e < C * C; e += NT) a.V[e] = Vw[(size_t)(e / C) * d.ldv + e % C];
+        for (int i = threadIdx.x; i < C; i += NT) a.S[i] = cb.S[i];
+    }
+    if (threadIdx.x == 0) {
+        a.out->accepted = o.accepted ? 1 : 0;
+        a.out->cay[0] = o.f1;
+        a.out->cay[1] = o.f2;
+        a.out->cay[2] = o.t;
+        a.out->cay[3] = o.f0;
+        a.out->cay[4] = o.ft;
+        a.out->status = 0;
+    }
 }
 
 cudaError_t configure_kernels(size_t max_smem) {
@@ -400,6 +440,11 @@ cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st) {
 
 cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st) {
     inner_step_kernel<<<1, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cayley_step(const CayArgs& a, cudaStream_t st) {
+    cayley_step_kernel<<<1, NT, smem_head_bytes(), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@ struct StepOut {
     int iters;            // inner
     int status;           // 0 ok, -2 singular G
     int reorth;           // svt: the warm start's V was re-orthonormalised in FP64
+    int accepted;         // cayley: the step was taken
+    double cay[5];        // cayley: f'(0), f''(0), t, f(0), f(t)
     double c1, c2, mu;    // inner
     double Q[3 * PMAX], G[PMAX * PMAX], Gi[PMAX * PMAX];
     double dtau[PMAX];
@@ -67,6 +69,7 @@ struct InnerArgs {
     float* Vg;
     float* Tg;
     float* Zg;     // scratch C * C
+    float* Cay;    // Algorithm 2 workspace (cayley_floats) when prm.svd_ws = 1, else nullptr
     int m, n, ttype, smem_svd;
     int use_q;     // 0: no constraint rows (G = J^T J, W^T W = J_perp)
     int jsched;    // Jacobi schedule
@@ -88,6 +91,16 @@ struct AdmArgs {
     float* Zg;         // scratch C * Cp
     int m, n, p, smem_svd, max_iter, jsched;
     double lam, tol, rho, mu0;
+    StepOut* out;
+};
+
+struct CayArgs {
+    const float* M;    // m x n, long-side layout (stride R)
+    float* U;          // R x C, stride R (in/out)
+    float* S;          // C (in/out)
+    float* V;          // C x C, stride C (in/out)
+    float* work;       // cayley_floats(d) + ldb * Cp + ldv * Cp floats of device memory
+    int m, n;
     StepOut* out;
 };
 
@@ -116,6 +129,7 @@ cudaError_t launch_gram_step(const GramArgs& a, cudaStream_t st);
 cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_adm_step(const AdmArgs& a, size_t smem, cudaStream_t st);
+cudaError_t launch_cayley_step(const CayArgs& a, cudaStream_t st);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t configure_kernels(size_t max_smem);
 

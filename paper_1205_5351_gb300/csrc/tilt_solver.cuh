@@ -2,6 +2,7 @@
 // loop of Algorithm 1, executed by one CTA per problem.
 #pragma once
 
+#include "tilt_cayley.cuh"
 #include "tilt_device.cuh"
 
 namespace tilt {
@@ -13,7 +14,7 @@ enum { FS_IMU = 0, FS_THR = 1, FS_MU = 2, FS_IMUN = 3, FS_CC = 8 };
 enum { LOOP_GO = 0, LOOP_CONVERGED = 1, LOOP_BAD = 2, LOOP_CANCELLED = 3 };
 
 struct InnerOut {
-    int iters, sweeps, warm, reorth, rank;
+    int iters, sweeps, warm, reorth, cayley, rank;
     bool converged, bad, cancelled, tc_timeout;
     double c1, c2, mu_last, nuc, l1;
 };
@@ -39,16 +40,45 @@ __device__ inline float soft(float x, float eps) {
 struct SvtStepOut {
     int sweeps;
     bool warm, tc_timeout, reorth;
+    bool cayley;                    // the SVD came from an accepted step of Algorithm 2
     unsigned long long t_svd_end;   // clock at the end of the SVD (start of the reconstruction)
 };
+
+// Kept singular values after a step of Algorithm 2: the signs of Sigma folded into U (so
+// Sigma >= 0), sigma_k = Sigma_k, w_k = (sigma_k - eps)_+, and the kept list, nuclear norm and
+// rank as svt_weights gives them.  All threads.
+static __device__ void svt_select_factors(const Dims& d, CayBufs cb, float eps, float* sigma, float* w, int* kept,
+                                          Scratch* sc) {
+    const int C = d.C, R = d.R, ldb = d.ldb;
+    for (int e = threadIdx.x; e < R * C; e += NT) {
+        const int k = e / R, r = e % R;
+        if (cb.S[k] < 0.f) cb.U[(size_t)k * ldb + r] = -cb.U[(size_t)k * ldb + r];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C; k += NT) {
+        const float s = fabsf(cb.S[k]);
+        cb.S[k] = s;
+        sigma[k] = s;
+        w[k] = s > eps ? s - eps : 0.f;
+    }
+    __syncthreads();
+    svt_select(C, eps, sigma, w, kept, sc);
+}
 
 // Singular value thresholding of the iteration's M (in buf.T): the one-sided Jacobi SVD,
 // warm-started from V when one exists, the gate allows and V has not drifted (a6), then
 // A' = S_eps(M) by the left-factor reconstruction (a7), stored into A with ||A' - A||^2 in
 // scal[7] and J^T A' in ja[] (FP64 totals of FP32 partials).  All threads.
+//
+// Algorithm 2 (cay != nullptr, a workspace of cayley_floats()): when the previous factors
+// exist (haveUS) and the gate allows, one Cayley step from them (cayley_step); if it is
+// accepted, A' = U(t) (Sigma(t) - eps)_+ V(t)^T directly and the Jacobi SVD is skipped;
+// otherwise, and on the first iteration, the full SVD runs and its factors are kept for the
+// next step.
 template <int NCH, bool TCP>
 static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& buf, const SmemLayout& L, bool& haveV, bool gate_ok,
-                                      float eps, float* __restrict__ A, const float* __restrict__ J, int jsched) {
+                                      float eps, float* __restrict__ A, const float* __restrict__ J, int jsched,
+                                      float* cay = nullptr, bool* haveUS = nullptr) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
     SvtStepOut so;
@@ -56,6 +86,47 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
     so.warm = false;
     so.tc_timeout = false;
     so.reorth = false;
+    so.cayley = false;
+    if (TCP && cay && *haveUS && gate_ok) {
+        CayBufs cb = carve_cayley(cay, d);
+        const CayleyOut co = cayley_step(d, buf.T, cb, buf.V, sc);
+        if (co.accepted) {
+            svt_select_factors(d, cb, eps, L.sigma, L.w, L.kept, sc);
+            so.cayley = true;
+            so.warm = true;
+            so.t_svd_end = clk();
+            const int nk = sc->iscal[1];
+            float acc[1 + PMAX];
+#pragma unroll
+            for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
+            auto upd = [&](int r, int c, float sa) {
+                const int e = c * R + r;
+                const float da = sa - A[e];
+                acc[0] = fmaf(da, da, acc[0]);
+                A[e] = sa;
+#pragma unroll
+                for (int k2 = 0; k2 < PMAX; ++k2)
+                    if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+            };
+            if (nk > 0) {
+                const float* Uc = cb.U;
+                const float* Vc = buf.V;
+                const float* wk = L.w;
+                const int* kept = L.kept;
+                gemm_simt<4, 4>(R, C, nk, [=](int r, int q) { return Uc[(size_t)kept[q] * ldb + r] * wk[kept[q]]; },
+                                [=](int q, int c) { return Vc[(size_t)kept[q] * ldv + c]; }, upd);
+            } else {
+                for (int e = threadIdx.x; e < S; e += NT) upd(e % R, e / R, 0.f);
+            }
+            block_sum_f<1 + PMAX>(acc, sc->red);
+            if (threadIdx.x == 0) {
+                sc->scal[7] = block_total(sc->red, 0);
+                for (int k2 = 0; k2 < p; ++k2) sc->ja[k2] = block_total(sc->red, 1 + k2);
+            }
+            __syncthreads();
+            return so;
+        }
+    }
     const bool warm = haveV && gate_ok;
     // FP32 rotations let V drift from orthogonal over many warm starts; past 1e-4 in a column
     // norm it is re-orthonormalised in FP64 and the warm start goes ahead
@@ -93,6 +164,18 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
     }
     haveV = true;
     svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);
+    if (TCP && cay) {
+        // the factors of this exact SVD, for the next step of Algorithm 2: U = B / sigma
+        CayBufs cb = carve_cayley(cay, d);
+        for (int e = threadIdx.x; e < ldb * C; e += NT) {
+            const int k = e / ldb, r = e % ldb;
+            const float sg = L.sigma[k];
+            cb.U[e] = (r < R && sg > 0.f) ? buf.B[(size_t)k * ldb + r] / sg : 0.f;
+        }
+        for (int k = threadIdx.x; k < C; k += NT) cb.S[k] = L.sigma[k];
+        __syncthreads();
+        *haveUS = true;
+    }
     so.t_svd_end = clk();
     // A' = sum_kept w_k b_k v_k^T
     const int nk = sc->iscal[1];
@@ -180,11 +263,14 @@ template <int NCH, bool TCP = true>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
                             float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
-                            bool& haveV, const SmemLayout& L, Result* cyc, int jsched, const int* cancel) {
+                            bool& haveV, const SmemLayout& L, Result* cyc, int jsched, const int* cancel,
+                            float* cay = nullptr) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, ldb = d.ldb;
+    bool haveUS = false;              // factors of a previous SVD of this inner loop (Algorithm 2)
+    float* cay_ws = (TCP && prm.svd_ws == 1) ? cay : nullptr;
     InnerOut out;
-    out.iters = 0; out.sweeps = 0; out.warm = 0; out.reorth = 0; out.rank = 0;
+    out.iters = 0; out.sweeps = 0; out.warm = 0; out.reorth = 0; out.cayley = 0; out.rank = 0;
     out.cancelled = false;
     out.converged = false; out.bad = false; out.tc_timeout = false;
     out.c1 = out.c2 = 0.0; out.mu_last = mu0; out.nuc = 0.0; out.l1 = 0.0;
@@ -274,11 +360,13 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         // ---- a6 + a7: SVD of M (in T), warm from V when the gate allows (Alg. 2 gate);
         // A' = S_{1/mu}(M); ||A' - A||^2 -> scal[7]; J^T A' -> ja
         t0 = clk();
-        const SvtStepOut so = svt_into<NCH, TCP>(d, buf, L, haveV, sc->iscal[6] != 0, sc->fs[FS_IMU], A, J, jsched);
+        const SvtStepOut so = svt_into<NCH, TCP>(d, buf, L, haveV, sc->iscal[6] != 0, sc->fs[FS_IMU], A, J, jsched,
+                                                 cay_ws, &haveUS);
         const unsigned long long t1 = so.t_svd_end;
         if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
         if (so.warm) out.warm++;
         if (so.reorth) out.reorth++;
+        if (so.cayley) out.cayley++;
         out.sweeps += so.sweeps;
         out.nuc = sc->scal[3];
         out.rank = sc->iscal[2];
@@ -622,7 +710,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
 
     int status = sc->iscal[7] ? -4 : 1;
     bool inner_maxed = false;
-    int outer = 0, inner_total = 0, sweeps = 0, warm = 0, reorth = 0, rank = 0;
+    int outer = 0, inner_total = 0, sweeps = 0, warm = 0, reorth = 0, cayley = 0, rank = 0;
     double c1 = 0.0, nuc = 0.0, l1 = 0.0;
     bool haveV = false;
 
@@ -657,11 +745,12 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
             if (threadIdx.x == 0) res.cyc_other += clk() - t1;
             InnerOut io = k_inner<NCH, TCP>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
-                                  pr.pl.Mp, buf, haveV, L, &res, pr.jsched, pr.cancel);
+                                  pr.pl.Mp, buf, haveV, L, &res, pr.jsched, pr.cancel, pr.pl.Cay);
             inner_total += io.iters;
             sweeps += io.sweeps;
             warm += io.warm;
             reorth += io.reorth;
+            cayley += io.cayley;
             c1 = io.c1; nuc = io.nuc; l1 = io.l1; rank = io.rank;
             if (io.tc_timeout) { status = -5; break; }
             if (io.bad) { status = -1; break; }
@@ -700,6 +789,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
         res.svd_sweeps = sweeps;
         res.svd_warm = warm;
         res.svd_reorth = reorth;
+        res.svd_cayley = cayley;
         res.oob_pixels = sc->iscal[0];
         res.kkt_residual = c1;
     }

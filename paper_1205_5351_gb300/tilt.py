@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("eps1", ctypes.c_double), ("eps2", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double),
                 ("eps_svd", ctypes.c_double), ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int),
-                ("outer_tol", ctypes.c_double)]
+                ("outer_tol", ctypes.c_double), ("svd_ws", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -50,7 +50,7 @@ class Result(ctypes.Structure):
                 ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("svd_sweeps", ctypes.c_int),
                 ("svd_warm", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("kkt_residual", ctypes.c_double),
                 ("latency_ms", ctypes.c_float), ("phase_cycles", ctypes.c_uint64 * 5),
-                ("launch_class", ctypes.c_int), ("svd_reorth", ctypes.c_int)]
+                ("launch_class", ctypes.c_int), ("svd_reorth", ctypes.c_int), ("svd_cayley", ctypes.c_int)]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Result":
@@ -66,7 +66,7 @@ class Result(ctypes.Structure):
                     inner_iters=self.inner_iters, svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm,
                     oob=self.oob_pixels, kkt=self.kkt_residual, latency_ms=self.latency_ms,
                     phase_cycles=list(self.phase_cycles), launch_class=self.launch_class,
-                    svd_reorth=self.svd_reorth)
+                    svd_reorth=self.svd_reorth, svd_cayley=self.svd_cayley)
 
 
 class Problem(ctypes.Structure):
@@ -98,6 +98,8 @@ SIGNATURES = {
     "tilt_inner": (_i, [_vp, _vp, _vp, _i, _i, _P(_d), _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d),
                         _P(_d), _P(_d), _P(_d)]),
     "tilt_svt_noalloc": (_i, [_vp, _i, _i, ctypes.c_float, _vp, _vp, _vp]),
+    "tilt_step_counters": (_i, [_vp, _P(_i), _P(_i)]),
+    "tilt_svd_cayley": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp, _P(_d), _P(_d), _P(_d), _P(_i)]),
     "tilt_svt_warm": (_i, [_vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _P(ctypes.c_float), _P(_i), _P(_i)]),
     "tilt_inner_adm": (_i, [_vp, _vp, _vp, _i, _i, _i, _P(Params), _d, _vp, _vp, _vp, _P(_i), _P(_d), _P(_d),
                             _P(_i)]),
@@ -335,6 +337,15 @@ class Context:
         _check(lib().tilt_svt(self.h, _dptr(M_t), m, n, float(eps), _dptr(A), sig, ctypes.byref(sw)), self.h)
         return A, np.array(sig, dtype=np.float32), sw.value
 
+    def svd_cayley(self, M_t, m: int, n: int, U_t, S_t, V_t) -> dict:
+        """tilt_svd_cayley: one Algorithm-2 step; U_t, S_t, V_t (CUDA, column-major) are updated in
+        place when the step is accepted."""
+        f1, f2, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        acc = ctypes.c_int()
+        _check(lib().tilt_svd_cayley(self.h, _dptr(M_t), m, n, _dptr(U_t), _dptr(S_t), _dptr(V_t), ctypes.byref(f1),
+                                     ctypes.byref(f2), ctypes.byref(t), ctypes.byref(acc)), self.h)
+        return dict(f1=f1.value, f2=f2.value, t=t.value, accepted=bool(acc.value))
+
     def svt_warm(self, M_t, m: int, n: int, eps: float, V_t):
         """tilt_svt_warm: V_t (CUDA, C x C column-major, C = min(m, n)) is the warm start and
         receives the new right singular vectors; returns (A, sigma, sweeps, reorth)."""
@@ -373,4 +384,7 @@ class Context:
                                 ctypes.byref(params) if params else None, float(mu0), _dptr(A_t), _dptr(E_t),
                                 _dptr(Y_t), ctypes.byref(it), dt, ctypes.byref(c1), ctypes.byref(c2),
                                 ctypes.byref(mu)), self.h)
-        return dict(iters=it.value, dtau=np.array(dt[:ttype]), c1=c1.value, c2=c2.value, mu=mu.value)
+        sw, cay = ctypes.c_int(), ctypes.c_int()
+        _check(lib().tilt_step_counters(self.h, ctypes.byref(sw), ctypes.byref(cay)), self.h)
+        return dict(iters=it.value, dtau=np.array(dt[:ttype]), c1=c1.value, c2=c2.value, mu=mu.value,
+                    sweeps=sw.value, cayley_steps=cay.value)

@@ -230,3 +230,58 @@ def test_warm_svt_reorthonormalises_a_drifted_v(T, ctx, seed, m, n):
         Vn = V_t.cpu().numpy().reshape(n, n).T.astype(np.float64)
         assert np.abs(Vn.T @ Vn - np.eye(n)).max() <= 1e-5
         assert sweeps < cold_sweeps
+
+
+@pytest.mark.parametrize("seed,m,n", [(71, 9, 6), (72, 64, 48), (73, 120, 100), (74, 40, 70)])
+def test_cayley_warm_start_step_parity(T, ctx, seed, m, n):
+    # one step of Algorithm 2 (Sec. 5, Appendix A) from the exact factors of a nearby matrix:
+    # f'(0), f''(0), t and the curve point U(t), Sigma(t), V(t) against the oracle's.  The
+    # step works on X (M, or M^T when m < n: U and V exchange roles)
+    rng = np.random.default_rng(seed)
+    M0 = rng.standard_normal((m, n))
+    M = (M0 + 0.03 * rng.standard_normal((m, n))).astype(np.float32)
+    X0 = M0 if m >= n else M0.T
+    X = M.astype(np.float64) if m >= n else M.T.astype(np.float64)
+    U0, s0, Vt0 = np.linalg.svd(X0, full_matrices=False)
+    U0, s0, V0 = U0.astype(np.float32).astype(np.float64), s0.astype(np.float32).astype(np.float64), \
+        Vt0.T.astype(np.float32).astype(np.float64)
+    _, _, _, f1, f2 = O.svdws_derivatives(X, U0, s0, V0)
+    ws = O.svd_warm_start(X, U0, s0, V0)
+    R, C = X.shape
+    U_t = torch.from_numpy(np.ascontiguousarray(U0.T).astype(np.float32).reshape(-1)).cuda()
+    S_t = torch.from_numpy(s0.astype(np.float32)).cuda()
+    V_t = torch.from_numpy(np.ascontiguousarray(V0.T).astype(np.float32).reshape(-1)).cuda()
+    out = ctx.svd_cayley(torch.from_numpy(T.to_long_layout(M)).cuda(), m, n, U_t, S_t, V_t)
+    assert abs(out["f1"] - f1) <= 1e-4 * abs(f1) and abs(out["f2"] - f2) <= 1e-4 * abs(f2), (out, f1, f2)
+    assert abs(out["t"] - (-f1 / f2)) <= 1e-4 * abs(f1 / f2)
+    assert out["accepted"] == (ws is not None)
+    Ut = U_t.cpu().numpy().reshape(C, R).T.astype(np.float64)
+    St = S_t.cpu().numpy().astype(np.float64)
+    Vt = V_t.cpu().numpy().reshape(C, C).T.astype(np.float64)
+    for got, want in ((Ut, ws[0]), (St, ws[1]), (Vt, ws[2]), ((Ut * St) @ Vt.T, (ws[0] * ws[1]) @ ws[2].T)):
+        assert rel(got, want) <= 1e-5, rel(got, want)
+    # the curve keeps the factors orthonormal (Sec. 5.1, property 2)
+    assert np.abs(Ut.T @ Ut - np.eye(C)).max() <= 1e-5 and np.abs(Vt.T @ Vt - np.eye(C)).max() <= 1e-5
+
+
+@pytest.mark.parametrize("seed,m,n,ttype", [(51, 50, 50, 6), (52, 64, 45, 8)])
+def test_inner_loop_with_the_papers_svd_warm_start(T, ctx, seed, m, n, ttype):
+    # the inner loop with Algorithm 2 (svd_ws = 1, gate eps_svd = 0.05) against the oracle's
+    # inner loop with the same warm start: the approximate SVDs change the trajectory (the
+    # oracle needs 129 / 135 iterations here against 60 / 56 with exact SVDs), and FP32 can
+    # flip a gate or acceptance decision that FP64 takes the other way, so iteration and
+    # step counts are compared to 10 % and A, E at 1e-3 relative
+    tau, Dh_d, J_d, Dh, J = _inner_inputs(T, ctx, seed, m, n, ttype)
+    mu0 = O.default_mu0(Dh)
+    A_d, E_d, Y_d = Dh_d.clone(), torch.zeros_like(Dh_d), torch.zeros_like(Dh_d)
+    out = ctx.inner(Dh_d, J_d, m, n, tau, ttype, T.default_params(svd_ws=1, eps_svd=0.05), mu0, A_d, E_d, Y_d)
+    Q = O.constraint_rows(tau, ttype, m, n)
+    lam = 1 / math.sqrt(max(m, n))
+    ref = O.inner_ladmap(Dh, J, Q, lam, Dh, 0 * Dh, 0 * Dh, O.Params(svd_warm=True, eps_svd=0.05), mu0=mu0)
+    assert ref.converged and ref.svd_warm_used > 0
+    assert abs(out["iters"] - ref.iters) <= max(3, ref.iters // 10), (out["iters"], ref.iters)
+    assert abs(out["cayley_steps"] - ref.svd_warm_used) <= max(3, ref.svd_warm_used // 10), \
+        (out["cayley_steps"], ref.svd_warm_used)
+    A = T.from_long_layout(A_d.cpu().numpy(), m, n)
+    E = T.from_long_layout(E_d.cpu().numpy(), m, n)
+    assert rel(A, ref.A) <= 1e-3 and rel(E, ref.E) <= 1e-3, (rel(A, ref.A), rel(E, ref.E))
