@@ -19,6 +19,10 @@ What it computes (paper section / equation named on every function):
   Eq. two_linear_constraint) and tau <- tau + dtau.
 * The comparison method of Sec. 2.2: the ADM of Zhang et al. for the inner loop
   (Eq. TILT_3), with the three blocks A, E, dtau updated in turn and mu <- rho mu.
+* RASL (Sec. 1): the same model with one image per column of the data matrix, so the
+  Jacobian of vec(D_hat) is block-diagonal (one block of p columns per image); the same
+  W^T W (with constraint rows that fix the set's mean transform), LADMAP inner loop and
+  outer loop.
 
 Readings of points where the paper is silent or inconsistent (each is listed in the
 design notes of the repository):
@@ -50,6 +54,18 @@ design notes of the repository):
 * R16 ADM (Sec. 2.2) parameters, not printed: mu_0 = 1.25/||D||_2, rho = 1.25, stop when
       ||D + J dtau - A - E||_F / ||D||_F < 1e-7 (the usual inexact-ALM settings of the cited
       line of work).
+* R18 RASL (Sec. 1 states only that it shares TILT's model with one image per column):
+      column i of D_hat is image i warped by tau_i over the m x n window (pixels in row-major
+      order) divided by its own Frobenius norm, J_i the Jacobian of that normalised column
+      (the quotient rule of Step 1, per column); the Jacobian of vec(D_hat) in the stacked
+      parameters is block-diagonal; additional constraints Q = [I_p ... I_p], i.e. the
+      increments dtau_i sum to zero: the low-rank objective cannot see a transform applied to
+      every image at once, and without these rows that common part of dtau swings by about a
+      pixel from one outer step to the next (TILT's Q fixes the window's position and size for
+      the same reason); W^T W and dtau as in Sec. 4.3 with these J and Q;
+      lambda = 1/sqrt(max(mn, N)); LADMAP parameters, warm starts and mu_0 as for TILT (R7,
+      R9); the outer loop stops when no window corner of any image moves by outer_tol pixels
+      (R8 per image).
 """
 from __future__ import annotations
 
@@ -313,7 +329,7 @@ def default_mu0(Dhat: np.ndarray) -> float:
 
 
 def inner_ladmap(Dhat, J, Q, lam, A0, E0, Yt0, prm: Params, mu0: float | None = None,
-                 trace: list | None = None) -> InnerResult:
+                 trace: list | None = None, op=None) -> InnerResult:
     """LADMAP for min ||A||_* + lam ||E||_1 s.t. W^T W (A + E) = W^T W D_hat
     (Eq. reformulated_TILT2), in the form of Eq. newvars2 with readings R1-R3, R7.
 
@@ -326,8 +342,9 @@ def inner_ladmap(Dhat, J, Q, lam, A0, E0, Yt0, prm: Params, mu0: float | None = 
         c1 = ||P_k+1||_F / d0,  c2 = mu_k max(||A_k+1 - A_k||_F, ||E_k+1 - E_k||_F) / d0,
         d0 = ||W^T W D_hat||_F; rho = rho0 if c2 < eps2 else 1; mu_k+1 = min(mu_max, rho mu_k)
     and the loop stops when c1 < eps1 and c2 < eps2 (Eqs. Cond1, Cond2).
+    ``op`` replaces WtW(J, Q) by a prepared operator (RASL: rasl_operator).
     """
-    op = WtW(J, Q)
+    op = WtW(J, Q) if op is None else op
     A = np.array(A0, dtype=np.float64)
     E = np.array(E0, dtype=np.float64)
     Yt = op(np.asarray(Yt0, dtype=np.float64))           # Eq. Y_new_warmstart
@@ -513,3 +530,93 @@ def objective(A, E, lam) -> float:
 
 def tau_error(tau, tau_ref) -> float:
     return float(np.linalg.norm(np.asarray(tau) - np.asarray(tau_ref)) / np.linalg.norm(tau_ref))
+
+
+# ============================================================================ RASL (Sec. 1)
+def rasl_warp(imgs, taus, ttype, m, n):
+    """Step 1 of Algorithm 1 for an image set (R18): D_hat (mn x N, column i = image i
+    warped by tau_i, normalised), the per-column Jacobians J_i (mn x p each), the norms
+    ||I_i o tau_i||_F and the total out-of-bounds count."""
+    cols, Js, norms = [], [], []
+    oob = 0
+    for img, tau in zip(imgs, taus):
+        Dhat_i, J_i, s_i, o_i = warp_normalise_jacobian(img, tau, ttype, m, n)
+        cols.append(Dhat_i.reshape(-1))
+        Js.append(J_i)
+        norms.append(s_i)
+        oob += o_i
+    return np.stack(cols, axis=1), Js, np.array(norms), oob
+
+
+def rasl_stacked_jacobian(Js) -> np.ndarray:
+    """The Jacobian of vec(D_hat) (row-major, entry r N + i for pixel r of image i) with
+    respect to the stacked parameters [tau_1; ...; tau_N] (entry i p + k): block-diagonal,
+    image i's block J_i (R18)."""
+    N = len(Js)
+    mn, p = Js[0].shape
+    Jb = np.zeros((mn * N, N * p))
+    for i, J in enumerate(Js):
+        Jb[i::N, i * p:(i + 1) * p] = J
+    return Jb
+
+
+def rasl_constraint_rows(N: int, p: int) -> np.ndarray:
+    """Q = [I_p ... I_p] (p x Np): the increments of the set's transforms sum to zero (R18)."""
+    return np.tile(np.eye(p), (1, N))
+
+
+def rasl_operator(Js) -> WtW:
+    """W^T W = I - J (J^T J + Q^T Q)^{-1} J^T (Eq. WTW_property) for the stacked,
+    block-diagonal Jacobian and the constraint rows of R18."""
+    N = len(Js)
+    p = Js[0].shape[1]
+    return WtW(rasl_stacked_jacobian(Js), rasl_constraint_rows(N, p))
+
+
+@dataclasses.dataclass
+class RaslResult:
+    tau: np.ndarray              # (N, p)
+    A: np.ndarray                # (mn, N)
+    E: np.ndarray
+    Dhat: np.ndarray             # D_hat at the last outer step's tau (before its update)
+    objective: float
+    rank: int
+    outer_iters: int
+    inner_iters: int
+    converged: bool
+    oob: int
+    inner_per_outer: list
+
+
+def rasl(imgs, taus0, ttype, m, n, prm: Params | None = None) -> RaslResult:
+    """Algorithm 1 for an image set (RASL, R18): warp every image by its tau_i, the LADMAP
+    inner loop with the column-wise W^T W and warm starts, dtau_i per image, until no
+    window corner moves by outer_tol pixels."""
+    prm = prm or Params()
+    taus = np.array(taus0, dtype=np.float64)
+    N = taus.shape[0]
+    lam = prm.lam if prm.lam > 0 else 1.0 / math.sqrt(max(m * n, N))
+    Dhat, Js, _, oob = rasl_warp(imgs, taus, ttype, m, n)
+    A = Dhat.copy()                                   # R9
+    E = np.zeros_like(Dhat)
+    Yt = np.zeros_like(Dhat)
+    inner_total = 0
+    per_outer = []
+    converged = False
+    i = 0
+    for i in range(1, prm.max_outer + 1):
+        if i > 1:
+            Dhat, Js, _, oob = rasl_warp(imgs, taus, ttype, m, n)
+        op = rasl_operator(Js)
+        res = inner_ladmap(Dhat, None, None, lam, A, E, Yt, prm, op=op)
+        A, E, Yt = res.A, res.E, res.Yt
+        inner_total += res.iters
+        per_outer.append(res.iters)
+        dtaus = op.coeffs(A + E - Dhat).reshape(N, -1)
+        shift = max(corner_shift(taus[k], dtaus[k], ttype, m, n) for k in range(N))
+        taus = taus + dtaus
+        if shift < prm.outer_tol:
+            converged = True
+            break
+    obj = nuclear_norm(A) + lam * float(np.abs(E).sum())
+    return RaslResult(taus, A, E, Dhat, obj, numerical_rank(A), i, inner_total, converged, oob, per_outer)

@@ -319,3 +319,80 @@ def random_inner_problem(rng: np.random.Generator, m: int, n: int, p: int = 6):
     D = rng.random((m, n))
     J = rng.standard_normal((m * n, p))
     return D, J
+
+
+# ----------------------------------------------------------------------------- RASL image sets
+@dataclasses.dataclass
+class RaslSet:
+    """One RASL problem: ``nimg`` images of the same low-rank scene, each seen through its
+    own transform, to be aligned jointly (one window of m x n pixels per image, the vectorised
+    windows forming the columns of the data matrix)."""
+
+    imgs: np.ndarray         # (nimg, H, W) float32 canvases, row-major
+    m: int                   # window rows
+    n: int                   # window columns
+    ttype: int               # AFFINE (6) or PROJECTIVE (8)
+    tau0: np.ndarray         # (nimg, p) float64 initial transforms
+    tau_true: np.ndarray     # (nimg, p) float64 transforms used to render the canvases
+    meta: dict
+
+    @property
+    def nimg(self) -> int:
+        return int(self.imgs.shape[0])
+
+    @property
+    def p(self) -> int:
+        return self.ttype
+
+
+def rasl_set(rng: np.random.Generator, nimg: int, m: int, n: int, *, rank: int = 2,
+             max_rot_deg: float = 3.0, max_scale: float = 0.03, max_shift: float = 1.5,
+             corruption: float = 0.02, noise_sigma: float = 0.0, ttype: int = AFFINE,
+             pad: int | None = None) -> RaslSet:
+    """Render ``nimg`` views of one rank-``rank`` texture.  View i shows
+    g_i T + o_i (gain g_i ~ U[0.6, 1.4], offset o_i ~ U[0, 0.2]: the aligned windows form a
+    matrix of rank <= 2) under the similarity s_i R(theta_i) with theta_i ~ U[-max_rot_deg,
+    max_rot_deg], s_i ~ 1 + U[-max_scale, max_scale] and a centre shifted by U[-max_shift,
+    max_shift] pixels on each axis, with a fraction ``corruption`` of its pixels replaced by
+    Uniform[0, 1] values (occlusion / specularity).  Every view starts from the same window,
+    centred on the canvas with the identity linear part."""
+    side = max(m, n)
+    pad = max(4, side // 2) if pad is None else int(pad)
+    H, W = m + 2 * pad, n + 2 * pad
+    cx, cy = (W - 1) / 2.0, (H - 1) / 2.0
+    cell = max(3.0, side / 6.0)
+    nknots = int(math.ceil(4 * (side + 2 * pad) / cell)) + 2
+    tex = LowRankTexture(rng, rank, cell, nknots)
+    gains = rng.uniform(0.6, 1.4, nimg)
+    offsets = rng.uniform(0.0, 0.2, nimg)
+    imgs = np.empty((nimg, H, W), dtype=np.float32)
+    p = ttype
+    tau_true = np.empty((nimg, p))
+    for i in range(nimg):
+        th = float(rng.uniform(-max_rot_deg, max_rot_deg))
+        s = 1.0 + float(rng.uniform(-max_scale, max_scale))
+        dx, dy = rng.uniform(-max_shift, max_shift, 2)
+        L = s * linear_part(th, 0.0)
+        img = gains[i] * _render(tex, H, W, L, cx + dx, cy + dy, (0.0, 0.0)) + offsets[i]
+        if noise_sigma > 0:
+            img = img + noise_sigma * rng.standard_normal(img.shape)
+        if corruption > 0:
+            mask = rng.random(img.shape) < corruption
+            img = np.where(mask, rng.random(img.shape), img)
+        imgs[i] = img
+        tau_true[i] = tau_vector(L, cx + dx, cy + dy, (0.0, 0.0), ttype)
+    tau0 = np.tile(tau_vector(np.eye(2), cx, cy, (0.0, 0.0), ttype), (nimg, 1))
+    meta = dict(rank=rank, max_rot_deg=max_rot_deg, max_scale=max_scale, max_shift=max_shift,
+                corruption=corruption, noise_sigma=noise_sigma, gains=gains, offsets=offsets)
+    return RaslSet(imgs, int(m), int(n), int(ttype), tau0, tau_true, meta)
+
+
+def rasl_batch(count: int = 152, first: int = 0, nimg: int = 32, side: int = 32,
+               ttype: int = AFFINE) -> list[RaslSet]:
+    """Independent RASL problems: ``nimg`` views of a rank-2 texture in ``side`` x ``side``
+    windows each (rotation +-3 deg, scale +-3 %, shift +-1.5 px, 2 % corrupted pixels)."""
+    out = []
+    for i in range(first, first + count):
+        rng = np.random.default_rng(seed_for(9, i))
+        out.append(rasl_set(rng, nimg, side, side, ttype=ttype))
+    return out
