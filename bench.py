@@ -120,7 +120,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream", "table1"], default="affine")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["stream", "table1", "rasl"], default="affine")
     ap.add_argument("--patches", type=int, default=None, help="patches per GPU (default: the workload's)")
     ap.add_argument("--plain-patches", type=int, default=8, help="patches in the plain GPU solver sample (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=30.0, help="budget of the oracle CPU sample")
@@ -134,6 +134,8 @@ def parse_args():
     ap.add_argument("--svd-ws", choices=["jacobi", "cayley"], default="jacobi",
                     help="SVD warm start: warm-started Jacobi (default) or the paper's Algorithm 2")
     ap.add_argument("--eps-svd", type=float, default=0.05, help="gate of Algorithm 2 (with --svd-ws cayley)")
+    ap.add_argument("--rasl-images", type=int, default=32, help="images per RASL set")
+    ap.add_argument("--rasl-side", type=int, default=32, help="window side of the RASL images")
     return ap.parse_args()
 
 
@@ -542,6 +544,186 @@ def run_ours(args, rank, world, local_rank, dist):
     return out
 
 
+# ----------------------------------------------------------------------------- RASL image sets
+RASL_WORKLOAD = ("RASL (Sec. 1): {count} independent image sets of {nimg} views of a rank-2 texture, "
+                 "{side}x{side} windows in {canvas}x{canvas} canvases, affine (p=6); each view under its own "
+                 "similarity (rotation +-3 deg, scale +-3 %, shift +-1.5 px), gain U[0.6, 1.4], offset "
+                 "U[0, 0.2], 2 % of the pixels replaced by Uniform[0, 1]")
+
+
+def _oracle_rasl(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import tilt_oracle as O
+    from paper_1205_5351_gb300 import synth
+    idx, nimg, side, max_outer = args
+    st = synth.rasl_batch(1, first=idx, nimg=nimg, side=side)[0]
+    t0 = time.perf_counter()
+    r = O.rasl(st.imgs.astype("float64"), st.tau0, st.ttype, st.m, st.n, O.Params(max_outer=max_outer))
+    return idx, time.perf_counter() - t0, r.tau.tolist(), r.inner_iters, r.rank
+
+
+def rasl_flops(R, C, r) -> float:
+    """FP32 work of one set's solve that the counters fix (as algorithmic_flops, with the data
+    matrix R = m n pixels by C = nimg images)."""
+    sweep = C * (C - 1) / 2 * (12 * R + 6 * C)
+    return r["svd_sweeps"] * sweep + r["svd_warm"] * 2.0 * R * C * C
+
+
+def run_rasl(args, rank, world, local_rank, dist):
+    """One step = the whole of Algorithm 1 for every image set of the batch (one launch, one
+    CTA per set), device-resident images; e2e: pinned host images in, tau, A and E out."""
+    import numpy as np
+    import torch
+
+    from paper_1205_5351_gb300 import multigpu, synth, tilt
+    count = args.patches or 152
+    nimg, side = args.rasl_images, args.rasl_side
+    pool = cores = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool, cores = cpu_pool()          # before any CUDA call
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    first = multigpu.first_index(count, rank)
+    sets = synth.rasl_batch(count, first=first, nimg=nimg, side=side)
+    imgs_h = np.stack([s.imgs for s in sets])
+    tau0 = np.stack([s.tau0 for s in sets])
+    imgs_d = torch.from_numpy(imgs_h).to(dev)
+    imgs_p = torch.from_numpy(imgs_h).pin_memory()
+    flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)       # the context's launches and the timing events share it
+    ctx = tilt.Context(local_rank, cuda_stream=stream.cuda_stream)
+    over = {k: v for k, v in (("max_outer", args.max_outer), ("max_inner", args.max_inner)) if v is not None}
+    params = tilt.default_params(**over)
+    m = n = side
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.rasl(imgs_d, m, n, tau0, 6, params)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times, kernel_ms, out_r = [], [], None
+    launches0 = ctx.launches
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        out_r = ctx.rasl(imgs_d, m, n, tau0, 6, params)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        kernel_ms.append(out_r["kernel_ms"])
+    launches = ctx.launches - launches0
+    clk = clocks.stop()
+    e2e_times = []
+    S = m * n * nimg
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        barrier()
+        t0 = time.perf_counter()
+        ctx.rasl(imgs_p, m, n, tau0, 6, params, planes=True)
+        e2e_times.append(1e3 * (time.perf_counter() - t0))
+    tot = multigpu.max_over_ranks([max(times), max(e2e_times)], dist, dev)
+    results = out_r["results"]
+    out = None
+    if rank == 0:
+        R, C = m * n, nimg
+        k_ms = statistics.mean(kernel_ms)
+        flops = sum(rasl_flops(R, C, r) for r in results)
+        props = torch.cuda.get_device_properties(dev)
+        n_sms = props.multi_processor_count
+        mhz = clk["sm_mhz"] or clk["sm_max_mhz"] or 2070.0
+        peak = n_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (k_ms * 1e-3) / 1e12
+        inner = sum(r["inner_iters"] for r in results)
+        cyc = [sum(r["phase_cycles"][i] for r in results) for i in range(5)]
+        value = count * world / (float(tot[0]) * 1e-3)
+        out = {
+            "metric": "RASL image sets aligned/s (and images/s, LADMAP iters/s)", "value": value,
+            "unit": "sets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": RASL_WORKLOAD.format(count=count, nimg=nimg, side=side,
+                                                        canvas=sets[0].imgs.shape[1]),
+                       "sets_per_gpu": count, "images_per_set": nimg, "window": [m, n], "p": 6,
+                       "l2": "512 MiB written before every step"},
+            "images_per_s": value * nimg,
+            "ladmap_iters_per_s": inner * world / (max(times) * 1e-3),
+            "status_counts": {str(s_): sum(1 for r in results if r["status"] == s_)
+                              for s_ in sorted({r["status"] for r in results})},
+            "inner_iters_per_set": inner / len(results),
+            "outer_iters_per_set": sum(r["outer_iters"] for r in results) / len(results),
+            "kcycles_per_inner_iter": round(sum(cyc) / max(1, inner) / 1e3, 2),
+            "svd": {"sweeps_per_svd": sum(r["svd_sweeps"] for r in results) / max(1, inner),
+                    "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner),
+                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results)},
+            "phase_split": dict(zip(["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"],
+                                    [round(c / max(1, sum(cyc)), 4) for c in cyc])),
+            "kernel_ms": k_ms,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "rasl_kernel (one CTA per image set, %d sets)" % count,
+                         "flops_per_launch": flops,
+                         "peak_source": "%d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz (median SM clock "
+                                        "sampled during the timed steps): FP32 FMA issue rate" % (n_sms, mhz)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": count * world / (float(tot[1]) * 1e-3), "unit": "sets/s",
+                    "h2d_bytes_per_step": int(imgs_h.nbytes + tau0.nbytes),
+                    "d2h_bytes_per_step": int(tau0.nbytes + 2 * 4 * S * count)},
+        }
+        if pool is not None:
+            def compare(sample, taus, res):
+                errs, rank_eq = [], 0
+                for idx, secs, tau, iters, rk in sample:
+                    q = idx - first
+                    tr = np.asarray(tau).ravel()
+                    errs.append(float(np.linalg.norm(taus[q].ravel() - tr) / np.linalg.norm(tr)))
+                    rank_eq += int(res[q]["rank"] == rk)
+                return errs, rank_eq
+
+            # CPU baseline: the oracle's full solve on the first sets of the batch
+            t0 = time.perf_counter()
+            full = []
+            nxt = 0
+            while nxt < count and time.perf_counter() - t0 < args.cpu_seconds:
+                batch = list(range(nxt, min(count, nxt + cores)))
+                full += pool.map(_oracle_rasl, [(first + q, nimg, side, params.max_outer) for q in batch])
+                nxt += len(batch)
+            wall = time.perf_counter() - t0
+            # parity: the same sets after three outer steps, on both sides (an untimed launch of
+            # the whole batch with max_outer = 3).  Most sets never meet the outer stopping rule:
+            # their last outer steps alternate between two transforms (a period-2 cycle of the
+            # Gauss-Newton step that both sides follow), and rounding moves the phase of that
+            # cycle, so the full solves agree only to a few 1e-3
+            short = pool.map(_oracle_rasl, [(first + q, nimg, side, 3) for q in range(len(full))])
+            pool.close()
+            gpu3 = ctx.rasl(imgs_d, m, n, tau0, 6, tilt.default_params(**{**over, "max_outer": 3}))
+            errs, rank_eq = compare(short, gpu3["tau"], gpu3["results"])
+            errs_f, rank_f = compare(full, out_r["tau"], results)
+            ok = sum(1 for e in errs if e <= 1e-3)
+            out["cpu_baseline"] = {"value": len(full) / wall if full else None, "unit": "sets/s",
+                                   "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                                   "sample": f"the first {len(full)} sets of the same batch (full solve), one per "
+                                             f"process, {wall:.1f} s wall"}
+            out["parity_sample"] = {"sets": len(errs), "tau_err_le_1e-3": ok, "rank_equal": rank_eq,
+                                    "max_tau_err": max(errs) if errs else None,
+                                    "selection": "the CPU-baseline sets, both sides stopped after 3 outer steps"}
+            out["full_solve_agreement"] = {
+                "sets": len(errs_f), "tau_err_le_1e-3": sum(1 for e in errs_f if e <= 1e-3),
+                "tau_err_le_1e-2": sum(1 for e in errs_f if e <= 1e-2), "rank_equal": rank_f,
+                "median_tau_err": float(np.median(errs_f)) if errs_f else None,
+                "max_tau_err": max(errs_f) if errs_f else None}
+            if errs:
+                out["value"] = value * ok / len(errs)
+    ctx.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- served stream
 def run_stream(args, rank, world, local_rank):
     """Poisson arrivals (--rate, 2000/s by default) of patches with sides 32..256, half affine / half projective,
@@ -714,6 +896,8 @@ def main():
         out = run_stream(args, rank, world, local_rank)
     elif args.workload == "table1":
         out = run_table1(args, rank)
+    elif args.workload == "rasl":
+        out = run_rasl(args, rank, world, local_rank, dist)
     else:
         out = run_ours(args, rank, world, local_rank, dist)
     if rank == 0 and out is not None:

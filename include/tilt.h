@@ -313,6 +313,46 @@ int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m,
 int tilt_step_counters(tilt_ctx* ctx, int* sweeps_out, int* cayley_steps_out);
 
 /* ------------------------------------------------------------------------------------------
+ * RASL (Sec. 1): the TILT model with one image per column of the data matrix.  An image set
+ * is nimg images of the same scene, each seen through its own transform tau_c; column c of
+ * D_hat is image c sampled at tau_c over an m x n window (pixel i, j at row i n + j of the
+ * column), divided by its own Frobenius norm, and J_c the Jacobian of that column with
+ * respect to tau_c, so the Jacobian of the stacked problem is block-diagonal.  Constraint
+ * rows Q = [I_p ... I_p] keep the sum of the increments dtau_c at zero (the low-rank
+ * objective cannot see a transform applied to every image at once).  Each set runs the whole
+ * of Algorithm 1 with this W^T W: the same LADMAP inner loop (Sec. 3.2, Eq. newvars2, warm
+ * starts of Eqs. warm_start and Y_new_warmstart, Cond1 and Cond2), dtau_c per image,
+ * tau_c <- tau_c + dtau_c, until no window corner of any image moves by outer_tol pixels.
+ * lambda <= 0 -> 1/sqrt(max(m n, nimg)). */
+typedef struct tilt_rasl_result {
+    int status;           /* as tilt_result.status (-2: a J_c^T J_c or the constraint system is singular) */
+    int outer_iters, inner_iters;
+    int svd_sweeps, svd_warm, svd_reorth;
+    int rank;             /* numerical rank of A (singular values > 1e-3 of the largest) */
+    int oob_pixels;       /* clamped samples at the last warp, over all images */
+    double objective;     /* ||A||_* + lambda ||E||_1 at exit */
+    double lambda;
+    double kkt_residual;  /* Cond1 value of the last inner iteration */
+    unsigned long long cycles[5];  /* SM cycles: warp, SVD, reconstruction, elementwise, other */
+} tilt_rasl_result;
+
+/* Solve `count` independent image sets of the same shape, one CTA per set, and wait for them
+ * (on the context's first stream, or the caller's stream of tilt_config.cuda_stream).
+ * imgs: count * nimg images of H x W floats, set s image c at imgs + (s nimg + c) H W, rows
+ * contiguous; device memory when is_device_ptr, else host memory (pinned for speed) that is
+ * copied to the device inside the call.  tau0, tau_out (host, may alias): count * nimg * p
+ * doubles, set s image c at (s nimg + c) p.  A_out, E_out, D_out (host, may be NULL): the
+ * result planes and the D_hat of the last outer step, count * nimg * m * n floats each,
+ * set s at offset s nimg m n, column c (image c) contiguous.  results (host): count records.
+ * kernel_ms_out (may be NULL): the launch's duration from CUDA events.  The device workspace
+ * (about (8 + p) nimg m n floats per set) is the context's scratch and grows on demand.
+ * Limits: 2 <= nimg <= 128, m n >= nimg, m, n, H, W >= 2, params->svd_ws = 0.  Errors:
+ * TILT_E_INVAL, TILT_E_CUDA. */
+int tilt_rasl(tilt_ctx* ctx, int count, int nimg, const float* imgs, int is_device_ptr, int H, int W, int m,
+              int n, tilt_transform type, const double* tau0, const tilt_params* params, double* tau_out,
+              float* A_out, float* E_out, float* D_out, tilt_rasl_result* results, float* kernel_ms_out);
+
+/* ------------------------------------------------------------------------------------------
  * Allocation-free singular value thresholding.  (The paper has no counterpart: this is a
  * service of the library, not a step of the method.)
  *

@@ -10,8 +10,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libtilt.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["tilt_kernels.cu", "tilt_api.cu", "tilt_noalloc.cu"]
-HEADERS = ["tilt_device.cuh", "tilt_solver.cuh", "tilt_launch.h"]
+SOURCES = ["tilt_kernels.cu", "tilt_kernels_tc.cu", "tilt_workers.cu", "tilt_steps.cu", "tilt_api.cu",
+           "tilt_noalloc.cu", "tilt_rasl.cu"]
+HEADERS = ["tilt_device.cuh", "tilt_solver.cuh", "tilt_launch.h", "tilt_tc.cuh", "tilt_cayley.cuh",
+           "tilt_rasl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

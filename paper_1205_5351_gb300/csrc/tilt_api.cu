@@ -166,6 +166,7 @@ struct tilt_ctx {
     StepOut* step_out_dev = nullptr;
     cudaEvent_t ev[6] = {};         // start/end events of the last grouped launches (3 classes)
     cudaEvent_t ev_copy[3] = {};    // end of the image uploads of a grouped submission, per stream
+    cudaEvent_t ev_rasl[2] = {};    // start/end of the last RASL launch
     int ev_used = 0;
     // persistent workers serving single submissions
     int num_sms = 0;
@@ -602,6 +603,7 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cfg->device));
     ctx->max_smem = (size_t)optin - 2048;    // static shared memory of the solver kernel
     CUDA_TRY(configure_kernels(ctx->max_smem));
+    CUDA_TRY(configure_rasl_kernels(ctx->max_smem));
     if (cfg->cuda_stream) {
         // the caller's stream carries every grouped launch, copy and step of this context
         ctx->own_streams = false;
@@ -629,6 +631,7 @@ int tilt_create(const tilt_config* cfg, tilt_ctx** out) {
     CUDA_TRY(cudaHostGetDevicePointer((void**)&ctx->step_out_dev, ctx->step_out, 0));
     for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
     for (auto& e : ctx->ev_copy) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : ctx->ev_rasl) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device));
     CUDA_TRY(cudaHostAlloc(&ctx->q_ring, ns * sizeof(int), cudaHostAllocMapped));
     CUDA_TRY(cudaHostAlloc(&ctx->q_ctl, 4 * sizeof(int), cudaHostAllocMapped));
@@ -1020,6 +1023,7 @@ int tilt_destroy(tilt_ctx* ctx) {
     }
     for (auto e : ctx->ev) cudaEventDestroy(e);
     for (auto e : ctx->ev_copy) cudaEventDestroy(e);
+    for (auto e : ctx->ev_rasl) cudaEventDestroy(e);
     cudaEventDestroy(ctx->worker_done);
     cudaStreamDestroy(ctx->worker_stream);
     cudaFree(ctx->q_head_dev);
@@ -1278,6 +1282,118 @@ int tilt_inner_adm(tilt_ctx* ctx, const float* D_dev, const float* J_dev, int m,
     if (dtau_out)
         for (int k = 0; k < p; ++k) dtau_out[k] = o.dtau[k];
     if (residual_out) *residual_out = o.c1;
+    return TILT_OK;
+}
+
+// ------------------------------------------------------------------------------ RASL
+int tilt_rasl(tilt_ctx* ctx, int count, int nimg, const float* imgs, int is_device_ptr, int H, int W, int m, int n,
+              tilt_transform type, const double* tau0, const tilt_params* params, double* tau_out, float* A_out,
+              float* E_out, float* D_out, tilt_rasl_result* results, float* kernel_ms_out) {
+    if (!ctx || (count > 0 && (!imgs || !tau0 || !tau_out || !results))) return fail(TILT_E_INVAL, "null argument");
+    if (count < 0) return fail(TILT_E_INVAL, "count = %d", count);
+    if (count == 0) {
+        if (kernel_ms_out) *kernel_ms_out = 0.f;
+        return TILT_OK;
+    }
+    if (type != TILT_AFFINE && type != TILT_PROJECTIVE) return fail(TILT_E_INVAL, "transform type %d", (int)type);
+    if (nimg < 2 || nimg > RASL_NMAX) return fail(TILT_E_INVAL, "%d images per set (2 .. %d)", nimg, RASL_NMAX);
+    if (m < 2 || n < 2 || H < 2 || W < 2) return fail(TILT_E_INVAL, "window %d x %d, images %d x %d", m, n, H, W);
+    if ((long long)m * n < nimg) return fail(TILT_E_INVAL, "window of %d pixels for %d images", m * n, nimg);
+    const Params prm = to_params(params);
+    if (!params_ok(prm) || prm.svd_ws != 0) return fail(TILT_E_INVAL, "parameters out of range");
+    const int p = (int)type;
+    for (size_t k = 0; k < (size_t)count * nimg * p; ++k)
+        if (!std::isfinite(tau0[k])) return fail(TILT_E_INVAL, "non-finite tau0");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    const Dims d = make_dims(m * n, nimg, p);
+    Layout L = plan(ctx, m * n, nimg, p, 0, 0, false, false);
+    if (jsched_order(L.jsched) != 2 && !ctx->force_js && !ctx->tune.count(size_bucket(d.R, d.C)))
+        L.jsched = rasl_schedule(d.R, d.C);
+    const size_t img_floats = (size_t)nimg * H * W;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += align_up(bytes); return r; };
+    const size_t per_set = align_up(L.total) + align_up((size_t)nimg * RASL_COLW * sizeof(double));
+    const size_t sets = take(per_set * count);
+    const size_t taus = take((size_t)count * nimg * p * sizeof(double));
+    const size_t probs = take((size_t)count * sizeof(RaslProblem));
+    const size_t resd = take((size_t)count * sizeof(RaslResult));
+    const size_t imgd = is_device_ptr ? 0 : take((size_t)count * img_floats * sizeof(float));
+    int rc = ensure_scratch(ctx, o);
+    if (rc) return rc;
+    char* base = static_cast<char*>(ctx->scratch);
+    cudaStream_t st = ctx->streams[0];
+    const float* imgs_dev = imgs;
+    if (!is_device_ptr) {
+        CUDA_TRY(cudaMemcpyAsync(base + imgd, imgs, (size_t)count * img_floats * sizeof(float), cudaMemcpyHostToDevice, st));
+        imgs_dev = reinterpret_cast<const float*>(base + imgd);
+    }
+    CUDA_TRY(cudaMemcpyAsync(base + taus, tau0, (size_t)count * nimg * p * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::vector<RaslProblem> hp(count);
+    for (int s = 0; s < count; ++s) {
+        char* b = base + sets + per_set * s;
+        RaslProblem& q = hp[s];
+        q.imgs = imgs_dev + img_floats * s;
+        q.img_stride = (long long)H * W;
+        q.ld = W;
+        q.H = H; q.W = W;
+        q.nimg = nimg; q.m = m; q.n = n; q.p = p; q.ttype = p;
+        q.prm = prm;
+        q.pl.Dhat = reinterpret_cast<float*>(b + L.dhat);
+        q.pl.J = reinterpret_cast<float*>(b + L.j);
+        q.pl.A = reinterpret_cast<float*>(b + L.a);
+        q.pl.E = reinterpret_cast<float*>(b + L.e);
+        q.pl.Y = reinterpret_cast<float*>(b + L.y);
+        q.pl.P = reinterpret_cast<float*>(b + L.p);
+        q.pl.Mp = reinterpret_cast<float*>(b + L.mp);
+        q.pl.Zg = reinterpret_cast<float*>(b + L.zg);
+        q.pl.Bg = (L.smem_svd & 1) ? nullptr : reinterpret_cast<float*>(b + L.bg);
+        q.pl.Vg = (L.smem_svd & 2) ? nullptr : reinterpret_cast<float*>(b + L.vg);
+        q.pl.Tg = (L.smem_svd & 4) ? nullptr : reinterpret_cast<float*>(b + L.tg);
+        q.pl.Cay = nullptr;
+        q.col = reinterpret_cast<double*>(b + align_up(L.total));
+        q.tau = reinterpret_cast<double*>(base + taus) + (size_t)s * nimg * p;
+        q.smem_svd = L.smem_svd;
+        q.jsched = L.jsched;
+        q.res = reinterpret_cast<RaslResult*>(base + resd) + s;
+    }
+    CUDA_TRY(cudaMemcpyAsync(base + probs, hp.data(), (size_t)count * sizeof(RaslProblem), cudaMemcpyHostToDevice, st));
+    const bool tcp = jsched_order(L.jsched) == 2;
+    CUDA_TRY(cudaEventRecord(ctx->ev_rasl[0], st));
+    CUDA_TRY(launch_rasl(reinterpret_cast<RaslProblem*>(base + probs), count, tcp, L.smem, st));
+    CUDA_TRY(cudaEventRecord(ctx->ev_rasl[1], st));
+    ctx->launches++;
+    std::vector<RaslResult> hr(count);
+    CUDA_TRY(cudaMemcpyAsync(hr.data(), base + resd, (size_t)count * sizeof(RaslResult), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(tau_out, base + taus, (size_t)count * nimg * p * sizeof(double), cudaMemcpyDeviceToHost, st));
+    const size_t plane = (size_t)d.S * sizeof(float);
+    for (int s = 0; s < count; ++s) {
+        const RaslProblem& q = hp[s];
+        if (A_out) CUDA_TRY(cudaMemcpyAsync(A_out + (size_t)d.S * s, q.pl.A, plane, cudaMemcpyDeviceToHost, st));
+        if (E_out) CUDA_TRY(cudaMemcpyAsync(E_out + (size_t)d.S * s, q.pl.E, plane, cudaMemcpyDeviceToHost, st));
+        if (D_out) CUDA_TRY(cudaMemcpyAsync(D_out + (size_t)d.S * s, q.pl.Dhat, plane, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (kernel_ms_out) CUDA_TRY(cudaEventElapsedTime(kernel_ms_out, ctx->ev_rasl[0], ctx->ev_rasl[1]));
+    for (int s = 0; s < count; ++s) {
+        const RaslResult& r = hr[s];
+        tilt_rasl_result& out = results[s];
+        out.status = r.status;
+        out.outer_iters = r.outer_iters;
+        out.inner_iters = r.inner_iters;
+        out.svd_sweeps = r.svd_sweeps;
+        out.svd_warm = r.svd_warm;
+        out.svd_reorth = r.svd_reorth;
+        out.rank = r.rank_A;
+        out.oob_pixels = r.oob_pixels;
+        out.objective = r.objective;
+        out.lambda = r.lambda;
+        out.kkt_residual = r.kkt_residual;
+        out.cycles[0] = r.cyc_warp;
+        out.cycles[1] = r.cyc_svd;
+        out.cycles[2] = r.cyc_recon;
+        out.cycles[3] = r.cyc_elem;
+        out.cycles[4] = r.cyc_other;
+    }
     return TILT_OK;
 }
 

@@ -76,6 +76,59 @@ struct Problem {
     const int* cancel;     // host-mapped: non-zero when the context is being destroyed
 };
 
+// ------------------------------------------------------------------------------ RASL
+// RASL (Sec. 1): TILT's model with one image per column of the data matrix.  An image set of
+// nimg images, each warped over an m x n window, gives an R x C matrix with R = m n pixels
+// (row-major within the window) and C = nimg columns, stored like a TILT plane (column c
+// contiguous); J holds, in column c, the Jacobian of that column with respect to tau_c.
+constexpr int RASL_NMAX = 128;      // images per set
+
+// FP64 state of one image of a set in device memory: a row of RASL_COLW doubles.
+enum {
+    RC_GI = 0,                      // (J_c^T J_c)^-1, p x p at row stride PMAX
+    RC_G = PMAX * PMAX,             // J_c^T J_c (Gram staging, then the matrix)
+    RC_JD = 2 * PMAX * PMAX,        // J_c^T D_hat_c
+    RC_B = RC_JD + PMAX,            // (J_c^T J_c)^-1 J_c^T x_c of the current W^T W product
+    RC_B2 = RC_B + PMAX,            // a second one (the prologue projects two planes at once)
+    RC_CV = RC_B2 + PMAX,           // coefficients of the last W^T W product (dtau_c at exit)
+    RC_TAU = RC_CV + PMAX,          // tau_c
+    RC_DD = RC_TAU + PMAX,          // ||D_hat_c||^2
+    RC_NORM = RC_DD + 1,            // ||I_c o tau_c||_F
+    RC_SHIFT = RC_NORM + 1,         // corner shift of the last update
+    RASL_COLW = RC_SHIFT + 2
+};
+
+struct RaslResult {
+    int status;
+    int outer_iters, inner_iters, svd_sweeps, svd_warm, svd_reorth, rank_A, oob_pixels;
+    double objective, lambda, kkt_residual;
+    unsigned long long cyc_warp, cyc_svd, cyc_recon, cyc_elem, cyc_other;
+};
+
+// One image set as the RASL kernel sees it.
+struct RaslProblem {
+    const float* imgs;     // image c at imgs + c * img_stride, rows at stride ld
+    long long img_stride, ld;
+    int H, W;
+    int nimg, m, n, p, ttype;
+    Params prm;
+    Planes pl;             // R = m n, C = nimg
+    double* col;           // nimg rows of RASL_COLW doubles
+    double* tau;           // nimg x p, tau0 on entry, the result on exit
+    int smem_svd, jsched;
+    RaslResult* res;
+};
+
+// Copy a small POD record word by word into shared memory (all threads).
+template <typename T>
+__device__ inline void copy_to_shared(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "record size");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(T) / 4); w += NT) d[w] = s[w];
+    __syncthreads();
+}
+
 // Non-zero once the host has asked running problems to stop (read by thread 0).
 __device__ inline int cancel_requested(const int* cancel) {
     if (!cancel) return 0;
@@ -307,6 +360,44 @@ __device__ inline void map_derivs(const MapPt& q, int ttype, double u, double v,
 }
 
 // ------------------------------------------------------------------------------ K1
+// Bilinear sample of img at the window point (u, v) mapped by tau, clamped at the image edge
+// (R5), with the raw Jacobian row J_k = I_x dx/dtau_k + I_y dy/dtau_k (Sec. 4.1 layout); the
+// derivative along a clamped axis is zero.  inside = false when a coordinate was clamped.
+__device__ __forceinline__ float warp_sample(const float* __restrict__ img, long long ld, int H, int W, int ttype,
+                                             const double* tau, double u, double v, float (&jr)[PMAX],
+                                             bool& inside) {
+    const double Wm1 = (double)(W - 1), Hm1 = (double)(H - 1);
+    MapPt q = map_point(tau, ttype, u, v);
+    const bool inx = (q.x >= 0.0) && (q.x <= Wm1);
+    const bool iny = (q.y >= 0.0) && (q.y <= Hm1);
+    const double xc = fmin(fmax(q.x, 0.0), Wm1);
+    const double yc = fmin(fmax(q.y, 0.0), Hm1);
+    const double x0 = fmin(floor(xc), (double)(W - 2));
+    const double y0 = fmin(floor(yc), (double)(H - 2));
+    const float fx = (float)(xc - x0), fy = (float)(yc - y0);
+    const long long xi = (long long)x0, yi = (long long)y0;
+    const float* row0 = img + yi * ld + xi;
+    const float I00 = __ldg(row0), I01 = __ldg(row0 + 1);
+    const float I10 = __ldg(row0 + ld), I11 = __ldg(row0 + ld + 1);
+    const float val = (1.f - fy) * ((1.f - fx) * I00 + fx * I01) + fy * ((1.f - fx) * I10 + fx * I11);
+    const float gx = inx ? ((1.f - fy) * (I01 - I00) + fy * (I11 - I10)) : 0.f;
+    const float gy = iny ? ((1.f - fx) * (I10 - I00) + fx * (I11 - I01)) : 0.f;
+    if (ttype == 8) {
+        const float iu = (float)(u / q.den), iv = (float)(v / q.den), i1 = (float)(1.0 / q.den);
+        const float gxy = gx * (float)q.x + gy * (float)q.y;
+        jr[0] = gx * iu; jr[1] = gx * iv; jr[2] = gx * i1;
+        jr[3] = gy * iu; jr[4] = gy * iv; jr[5] = gy * i1;
+        jr[6] = -gxy * iu; jr[7] = -gxy * iv;
+    } else {
+        const float uf = (float)u, vf = (float)v;
+        jr[0] = gx * uf; jr[1] = gx * vf; jr[2] = gx;
+        jr[3] = gy * uf; jr[4] = gy * vf; jr[5] = gy;
+        jr[6] = 0.f; jr[7] = 0.f;
+    }
+    inside = inx && iny;
+    return val;
+}
+
 // Algorithm 1, Step 1: warp + normalise + Jacobian of the normalised warp.
 // Writes D_hat and J; returns ||D o tau||_F (scal[0]) and the clamped-sample count (iscal[0]).
 static __device__ void k1_warp_jacobian(const float* __restrict__ img, long long ld, int H, int W,
@@ -314,7 +405,6 @@ static __device__ void k1_warp_jacobian(const float* __restrict__ img, long long
                                  float* __restrict__ Dhat, float* __restrict__ J, Scratch* sc) {
     const int p = d.p, S = d.S;
     const double hm = 0.5 * (d.m - 1), hn = 0.5 * (d.n - 1);
-    const double Wm1 = (double)(W - 1), Hm1 = (double)(H - 1);
     double acc[2 + PMAX];
 #pragma unroll
     for (int k = 0; k < 2 + PMAX; ++k) acc[k] = 0.0;
@@ -322,38 +412,12 @@ static __device__ void k1_warp_jacobian(const float* __restrict__ img, long long
         int i, j;
         pixel_of(d, e, i, j);
         const double u = (double)j - hn, v = (double)i - hm;
-        MapPt q = map_point(tau, ttype, u, v);
-        const bool inx = (q.x >= 0.0) && (q.x <= Wm1);
-        const bool iny = (q.y >= 0.0) && (q.y <= Hm1);
-        const double xc = fmin(fmax(q.x, 0.0), Wm1);
-        const double yc = fmin(fmax(q.y, 0.0), Hm1);
-        const double x0 = fmin(floor(xc), (double)(W - 2));
-        const double y0 = fmin(floor(yc), (double)(H - 2));
-        const float fx = (float)(xc - x0), fy = (float)(yc - y0);
-        const long long xi = (long long)x0, yi = (long long)y0;
-        const float* row0 = img + yi * ld + xi;
-        const float I00 = __ldg(row0), I01 = __ldg(row0 + 1);
-        const float I10 = __ldg(row0 + ld), I11 = __ldg(row0 + ld + 1);
-        const float val = (1.f - fy) * ((1.f - fx) * I00 + fx * I01) + fy * ((1.f - fx) * I10 + fx * I11);
-        const float gx = inx ? ((1.f - fy) * (I01 - I00) + fy * (I11 - I10)) : 0.f;
-        const float gy = iny ? ((1.f - fx) * (I10 - I00) + fx * (I11 - I01)) : 0.f;
-        // raw Jacobian row: J_k = I_x dx/dtau_k + I_y dy/dtau_k (Sec. 4.1 layout)
         float jr[PMAX];
-        if (ttype == 8) {
-            const float iu = (float)(u / q.den), iv = (float)(v / q.den), i1 = (float)(1.0 / q.den);
-            const float gxy = gx * (float)q.x + gy * (float)q.y;
-            jr[0] = gx * iu; jr[1] = gx * iv; jr[2] = gx * i1;
-            jr[3] = gy * iu; jr[4] = gy * iv; jr[5] = gy * i1;
-            jr[6] = -gxy * iu; jr[7] = -gxy * iv;
-        } else {
-            const float uf = (float)u, vf = (float)v;
-            jr[0] = gx * uf; jr[1] = gx * vf; jr[2] = gx;
-            jr[3] = gy * uf; jr[4] = gy * vf; jr[5] = gy;
-            jr[6] = 0.f; jr[7] = 0.f;
-        }
+        bool inside;
+        const float val = warp_sample(img, ld, H, W, ttype, tau, u, v, jr, inside);
         Dhat[e] = val;
         acc[0] += (double)val * (double)val;
-        acc[1] += (inx && iny) ? 0.0 : 1.0;
+        acc[1] += inside ? 0.0 : 1.0;
 #pragma unroll
         for (int k = 0; k < PMAX; ++k) {
             if (k < p) {
@@ -1056,6 +1120,15 @@ __host__ __device__ inline int staged_block(const Dims& d, size_t avail) {
 // buckets; round-robin width 4 was 1.4x slower on 200 x 200 windows.)
 __host__ __device__ inline int default_schedule(int R, int C) {
     return ((R > 128 && C >= 64) ? 16 : 8) | JSCHED_BLOCK;
+}
+
+// Schedule of a RASL set (long columns of m n pixels, one per image) whose size bucket the
+// autotuner has not timed: block-cyclic, 16 lanes per pair once the columns are 256 long
+// (measured on 32 x 32 windows of 32 images: 0.83x the SVD cycles per iteration of width 8,
+// 0.41x of width 4).
+__host__ __device__ inline int rasl_schedule(int R, int C) {
+    (void)C;
+    return (R >= 256 ? 16 : 8) | JSCHED_BLOCK;
 }
 
 // The kept columns (w_k > 0) in ascending order, sum and max of (sigma_k - eps)_+ over them

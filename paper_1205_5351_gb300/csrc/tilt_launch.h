@@ -130,8 +130,17 @@ cudaError_t launch_svt_step(const SvtArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_inner_step(const InnerArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_adm_step(const AdmArgs& a, size_t smem, cudaStream_t st);
 cudaError_t launch_cayley_step(const CayArgs& a, cudaStream_t st);
+// RASL image sets: count CTAs, CTA b solves probs[b] (tcp: the variant with the staged
+// Jacobi sweeps).
+cudaError_t launch_rasl(RaslProblem* probs, int count, bool tcp, size_t smem, cudaStream_t st);
 // One-time kernel attribute setup (dynamic shared memory opt-in).
 cudaError_t configure_kernels(size_t max_smem);
+cudaError_t configure_tc_kernels(size_t max_smem);
+cudaError_t configure_worker_kernel(size_t max_smem);
+cudaError_t configure_step_kernels(size_t max_smem);
+cudaError_t configure_rasl_kernels(size_t max_smem);
+// The tensor-core variant of the solver (launch class 2), called by launch_solver.
+cudaError_t launch_solver_tc(Problem* probs, const int* order, int count, size_t smem, cudaStream_t st);
 
 // Record an error message for tilt_last_error() on the calling thread; returns code.
 int set_error(int code, const char* msg);

@@ -796,4 +796,27 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
     __syncthreads();
 }
 
+// One CTA per problem: the whole of Algorithm 1.  The result record and the completion
+// flag live in host-mapped memory, so the host sees every problem retire on its own.
+// MINB CTAs per SM; NCH float4 chunks per lane keep a Jacobi column pair in registers
+// (R <= 32 NCH), fewer for the 2-CTA variant so that it fits 64 registers per thread.
+// TCP: the kernel carries the tensor-core path (only the launch class of large windows: the
+// extra code costs the SIMT path registers).
+template <int MINB, int NCH, bool TCP>
+__global__ void __launch_bounds__(NT, MINB) solver_kernel(Problem* probs, const int* order) {
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    __shared__ Problem sp;
+    __shared__ Result sres;
+    SmemLayout L = carve_smem(smem_raw);
+    if (TCP) tc_setup(&L.sc->tc, TC_TMEM_COLS);
+    copy_to_shared(&sp, probs + order[blockIdx.x]);
+    solve_problem<NCH, TCP>(sp, L, sres);
+    if (threadIdx.x == 0) {
+        *sp.res = sres;
+        __threadfence_system();
+        *sp.done = 1;
+    }
+    if (TCP) tc_teardown(&L.sc->tc, TC_TMEM_COLS);
+}
+
 }  // namespace tilt

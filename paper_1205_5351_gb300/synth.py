@@ -348,7 +348,7 @@ class RaslSet:
 def rasl_set(rng: np.random.Generator, nimg: int, m: int, n: int, *, rank: int = 2,
              max_rot_deg: float = 3.0, max_scale: float = 0.03, max_shift: float = 1.5,
              corruption: float = 0.02, noise_sigma: float = 0.0, ttype: int = AFFINE,
-             pad: int | None = None) -> RaslSet:
+             pad: int | None = None, cell: float | None = None) -> RaslSet:
     """Render ``nimg`` views of one rank-``rank`` texture.  View i shows
     g_i T + o_i (gain g_i ~ U[0.6, 1.4], offset o_i ~ U[0, 0.2]: the aligned windows form a
     matrix of rank <= 2) under the similarity s_i R(theta_i) with theta_i ~ U[-max_rot_deg,
@@ -360,7 +360,7 @@ def rasl_set(rng: np.random.Generator, nimg: int, m: int, n: int, *, rank: int =
     pad = max(4, side // 2) if pad is None else int(pad)
     H, W = m + 2 * pad, n + 2 * pad
     cx, cy = (W - 1) / 2.0, (H - 1) / 2.0
-    cell = max(3.0, side / 6.0)
+    cell = max(3.0, side / 6.0) if cell is None else float(cell)
     nknots = int(math.ceil(4 * (side + 2 * pad) / cell)) + 2
     tex = LowRankTexture(rng, rank, cell, nknots)
     gains = rng.uniform(0.6, 1.4, nimg)

@@ -69,6 +69,19 @@ class Result(ctypes.Structure):
                     svd_reorth=self.svd_reorth, svd_cayley=self.svd_cayley)
 
 
+class RaslResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("svd_sweeps", ctypes.c_int), ("svd_warm", ctypes.c_int), ("svd_reorth", ctypes.c_int),
+                ("rank", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("objective", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("kkt_residual", ctypes.c_double), ("cycles", ctypes.c_uint64 * 5)]
+
+    def to_dict(self) -> dict:
+        return dict(status=self.status, outer_iters=self.outer_iters, inner_iters=self.inner_iters,
+                    svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm, svd_reorth=self.svd_reorth,
+                    rank=self.rank, oob=self.oob_pixels, objective=self.objective, lam=self.lambda_,
+                    kkt=self.kkt_residual, phase_cycles=list(self.cycles))
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("img", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int), ("ld_elems", ctypes.c_size_t),
                 ("m", ctypes.c_int), ("n", ctypes.c_int), ("type", ctypes.c_int), ("tau0", ctypes.c_double * 8)]
@@ -105,6 +118,8 @@ SIGNATURES = {
                             _P(_i)]),
     "tilt_best_of": (_i, [_P(Result), _i, _i, _P(_i)]),
     "tilt_autotune": (_i, [_vp, _P(_i), _i, _i, _P(_i)]),
+    "tilt_rasl": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _i, _i, _i, _P(_d), _P(Params), _P(_d), _vp, _vp, _vp,
+                       _P(RaslResult), _P(ctypes.c_float)]),
 }
 
 _lib = None
@@ -372,6 +387,42 @@ class Context:
                                     ctypes.byref(params) if params else None, float(mu0), _dptr(A), _dptr(E),
                                     _dptr(Y), ctypes.byref(it), dt, ctypes.byref(res), ctypes.byref(sw)), self.h)
         return dict(A=A, E=E, Y=Y, iters=it.value, dtau=np.array(dt[:p]), residual=res.value, sweeps=sw.value)
+
+    def rasl(self, imgs, m: int, n: int, tau0, ttype: int, params: Params | None = None,
+             planes: bool = False) -> dict:
+        """tilt_rasl on a batch of image sets.  ``imgs``: (count, nimg, H, W) float32, a numpy
+        array or a contiguous host (e.g. pinned) or CUDA tensor; ``tau0``: (count, nimg, p).
+        Returns tau (count, nimg, p), the result records, the launch's kernel time and, when
+        ``planes``, A, E and D_hat as (count, m n, nimg) arrays (column c = image c)."""
+        if hasattr(imgs, "data_ptr"):
+            assert imgs.is_contiguous() and str(imgs.dtype) == "torch.float32"
+            count, nimg, H, W = (int(v) for v in imgs.shape)
+            ptr, on_dev = imgs.data_ptr(), 1 if imgs.is_cuda else 0
+            keep = imgs
+        else:
+            keep = np.ascontiguousarray(imgs, dtype=np.float32)
+            count, nimg, H, W = keep.shape
+            ptr, on_dev = keep.ctypes.data, 0
+        p = int(ttype)
+        t0 = np.ascontiguousarray(np.asarray(tau0, dtype=np.float64).reshape(count, nimg, p))
+        tau = np.empty_like(t0)
+        res = (RaslResult * max(count, 1))()
+        S = m * n * nimg
+        A = np.empty((count, S), np.float32) if planes else None
+        E = np.empty((count, S), np.float32) if planes else None
+        D = np.empty((count, S), np.float32) if planes else None
+        ms = ctypes.c_float()
+        dp = lambda a: a.ctypes.data if a is not None else None
+        _check(lib().tilt_rasl(self.h, count, nimg, ptr, on_dev, H, W, m, n, ttype,
+                               t0.ctypes.data_as(_P(_d)), ctypes.byref(params) if params else None,
+                               tau.ctypes.data_as(_P(_d)), dp(A), dp(E), dp(D), res, ctypes.byref(ms)), self.h)
+        del keep
+        out = dict(tau=tau, results=[res[i].to_dict() for i in range(count)], kernel_ms=ms.value)
+        if planes:
+            shape = (count, nimg, m * n)
+            out.update(A=A.reshape(shape).transpose(0, 2, 1), E=E.reshape(shape).transpose(0, 2, 1),
+                       Dhat=D.reshape(shape).transpose(0, 2, 1))
+        return out
 
     def inner(self, Dhat_t, J_t, m: int, n: int, tau, ttype: int, params: Params | None, mu0: float,
               A_t, E_t, Y_t) -> dict:
