@@ -695,15 +695,20 @@ def run_rasl(args, rank, world, local_rank, dist):
                 full += pool.map(_oracle_rasl, [(first + q, nimg, side, params.max_outer) for q in batch])
                 nxt += len(batch)
             wall = time.perf_counter() - t0
-            # parity: the same sets after three outer steps, on both sides (an untimed launch of
-            # the whole batch with max_outer = 3).  Most sets never meet the outer stopping rule:
-            # their last outer steps alternate between two transforms (a period-2 cycle of the
-            # Gauss-Newton step that both sides follow), and rounding moves the phase of that
-            # cycle, so the full solves agree only to a few 1e-3
-            short = pool.map(_oracle_rasl, [(first + q, nimg, side, 3) for q in range(len(full))])
+            # parity: the same sets after one outer step (warp, Gram blocks, the whole inner loop,
+            # dtau, tau update) on both sides, in untimed launches of the whole batch; three
+            # outer steps and the full solves are reported beside it.  Most sets never meet the
+            # outer stopping rule: their last outer steps alternate between two transforms (a
+            # period-2 cycle of the Gauss-Newton step that both sides follow), rounding moves
+            # the phase of that cycle, and the FP32 and FP64 trajectories drift apart from one
+            # outer step to the next
+            one = pool.map(_oracle_rasl, [(first + q, nimg, side, 1) for q in range(len(full))])
+            three = pool.map(_oracle_rasl, [(first + q, nimg, side, 3) for q in range(len(full))])
             pool.close()
+            gpu1 = ctx.rasl(imgs_d, m, n, tau0, 6, tilt.default_params(**{**over, "max_outer": 1}))
             gpu3 = ctx.rasl(imgs_d, m, n, tau0, 6, tilt.default_params(**{**over, "max_outer": 3}))
-            errs, rank_eq = compare(short, gpu3["tau"], gpu3["results"])
+            errs, rank_eq = compare(one, gpu1["tau"], gpu1["results"])
+            errs_3, rank_3 = compare(three, gpu3["tau"], gpu3["results"])
             errs_f, rank_f = compare(full, out_r["tau"], results)
             ok = sum(1 for e in errs if e <= 1e-3)
             out["cpu_baseline"] = {"value": len(full) / wall if full else None, "unit": "sets/s",
@@ -712,7 +717,11 @@ def run_rasl(args, rank, world, local_rank, dist):
                                              f"process, {wall:.1f} s wall"}
             out["parity_sample"] = {"sets": len(errs), "tau_err_le_1e-3": ok, "rank_equal": rank_eq,
                                     "max_tau_err": max(errs) if errs else None,
-                                    "selection": "the CPU-baseline sets, both sides stopped after 3 outer steps"}
+                                    "selection": "the CPU-baseline sets, both sides stopped after one outer step"}
+            out["three_step_agreement"] = {
+                "sets": len(errs_3), "tau_err_le_1e-3": sum(1 for e in errs_3 if e <= 1e-3), "rank_equal": rank_3,
+                "median_tau_err": float(np.median(errs_3)) if errs_3 else None,
+                "max_tau_err": max(errs_3) if errs_3 else None}
             out["full_solve_agreement"] = {
                 "sets": len(errs_f), "tau_err_le_1e-3": sum(1 for e in errs_f if e <= 1e-3),
                 "tau_err_le_1e-2": sum(1 for e in errs_f if e <= 1e-2), "rank_equal": rank_f,
