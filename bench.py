@@ -563,8 +563,16 @@ def _oracle_rasl(args):
 
 
 def rasl_flops(R, C, r) -> float:
-    """FP32 work of one set's solve that the counters fix (as algorithmic_flops, with the data
-    matrix R = m n pixels by C = nimg images)."""
+    """FP32 work of one set's SVTs that the counters fix, for the data matrix R = m n pixels by
+    C = nimg images.  One-sided Jacobi on M (as algorithmic_flops): sweeps x C(C-1)/2 x
+    (12 R + 6 C) plus 2 R C^2 per warm start.  QR path: per iteration the Householder QR
+    (2 R C^2 - 2 C^3 / 3), the reflectors' Gram (R C^2) and the product with them (2 R C^2),
+    sweeps x C(C-1)/2 x 18 C on the C x C factor, C^3 per warm start and 4 C^3 for the small
+    products of the reconstruction."""
+    if r.get("svt_qr"):
+        it = r["inner_iters"]
+        return (it * (5.0 * R * C * C - 2.0 * C ** 3 / 3 + 4.0 * C ** 3) + r["svd_warm"] * float(C ** 3)
+                + r["svd_sweeps"] * C * (C - 1) / 2 * 18.0 * C)
     sweep = C * (C - 1) / 2 * (12 * R + 6 * C)
     return r["svd_sweeps"] * sweep + r["svd_warm"] * 2.0 * R * C * C
 
@@ -660,7 +668,9 @@ def run_rasl(args, rank, world, local_rank, dist):
             "kcycles_per_inner_iter": round(sum(cyc) / max(1, inner) / 1e3, 2),
             "svd": {"sweeps_per_svd": sum(r["svd_sweeps"] for r in results) / max(1, inner),
                     "warm_fraction": sum(r["svd_warm"] for r in results) / max(1, inner),
-                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results)},
+                    "fp64_reorthonormalisations": sum(r["svd_reorth"] for r in results),
+                    "path": "QR, then one-sided Jacobi of the %dx%d factor" % (C, C)
+                            if all(r["svt_qr"] for r in results) else "one-sided Jacobi of M"},
             "phase_split": dict(zip(["warp_jacobian", "svd", "svt_reconstruct", "elementwise", "other"],
                                     [round(c / max(1, sum(cyc)), 4) for c in cyc])),
             "kernel_ms": k_ms,

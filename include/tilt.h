@@ -323,13 +323,22 @@ int tilt_step_counters(tilt_ctx* ctx, int* sweeps_out, int* cayley_steps_out);
  * of Algorithm 1 with this W^T W: the same LADMAP inner loop (Sec. 3.2, Eq. newvars2, warm
  * starts of Eqs. warm_start and Y_new_warmstart, Cond1 and Cond2), dtau_c per image,
  * tau_c <- tau_c + dtau_c, until no window corner of any image moves by outer_tol pixels.
- * lambda <= 0 -> 1/sqrt(max(m n, nimg)). */
+ * lambda <= 0 -> 1/sqrt(max(m n, nimg)).
+ *
+ * SVT of a tall set (m n >= 4 nimg + 4, M small enough for shared memory: about 200 KB for M,
+ * V and the buffers, e.g. 32 images of 32 x 32): M = Q R by Householder reflectors, the
+ * one-sided Jacobi SVD of the nimg x nimg matrix R V (warm from the previous V), and
+ * S_eps(M) = Q X with X formed from R's SVD (X = sum over kept k of (w_k / sigma_k^2) b_k
+ * (R^T b_k)^T, b_k the columns of R V after the sweeps), Q applied in the compact WY form.
+ * Other sets run the one-sided Jacobi on M itself, as TILT does. */
 typedef struct tilt_rasl_result {
     int status;           /* as tilt_result.status (-2: a J_c^T J_c or the constraint system is singular) */
     int outer_iters, inner_iters;
     int svd_sweeps, svd_warm, svd_reorth;
     int rank;             /* numerical rank of A (singular values > 1e-3 of the largest) */
     int oob_pixels;       /* clamped samples at the last warp, over all images */
+    int svt_qr;           /* 1: the SVTs ran through the QR factorisation of M (tall sets whose M fits
+                           * in shared memory; see below), 0: one-sided Jacobi on M itself */
     double objective;     /* ||A||_* + lambda ||E||_1 at exit */
     double lambda;
     double kkt_residual;  /* Cond1 value of the last inner iteration */

@@ -1309,6 +1309,15 @@ int tilt_rasl(tilt_ctx* ctx, int count, int nimg, const float* imgs, int is_devi
     Layout L = plan(ctx, m * n, nimg, p, 0, 0, false, false);
     if (jsched_order(L.jsched) != 2 && !ctx->force_js && !ctx->tune.count(size_bucket(d.R, d.C)))
         L.jsched = rasl_schedule(d.R, d.C);
+    // tall data matrices whose M fits in shared memory with V, B_c and the small buffers take
+    // the SVT's QR path (svt_tall_qr); its buffers are carved by the kernel, not by plan()
+    const size_t tall_smem = smem_head_bytes() + sizeof(float) * ((size_t)d.ldv * d.Cp + (size_t)d.ldb * d.Cp +
+                                                                  (size_t)d.C * d.Cp + tall_small_floats(d));
+    const bool tall = tall_qr_ok(d) && tall_smem <= ctx->max_smem;
+    if (tall) {
+        L.smem = tall_smem;
+        if (jsched_order(L.jsched) == 2) L.jsched = rasl_schedule(d.R, d.C);
+    }
     const size_t img_floats = (size_t)nimg * H * W;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += align_up(bytes); return r; };
@@ -1354,6 +1363,7 @@ int tilt_rasl(tilt_ctx* ctx, int count, int nimg, const float* imgs, int is_devi
         q.tau = reinterpret_cast<double*>(base + taus) + (size_t)s * nimg * p;
         q.smem_svd = L.smem_svd;
         q.jsched = L.jsched;
+        q.tall = tall ? 1 : 0;
         q.res = reinterpret_cast<RaslResult*>(base + resd) + s;
     }
     CUDA_TRY(cudaMemcpyAsync(base + probs, hp.data(), (size_t)count * sizeof(RaslProblem), cudaMemcpyHostToDevice, st));
@@ -1385,6 +1395,7 @@ int tilt_rasl(tilt_ctx* ctx, int count, int nimg, const float* imgs, int is_devi
         out.svd_reorth = r.svd_reorth;
         out.rank = r.rank_A;
         out.oob_pixels = r.oob_pixels;
+        out.svt_qr = r.svt_qr;
         out.objective = r.objective;
         out.lambda = r.lambda;
         out.kkt_residual = r.kkt_residual;

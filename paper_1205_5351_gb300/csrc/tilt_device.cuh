@@ -101,6 +101,7 @@ enum {
 struct RaslResult {
     int status;
     int outer_iters, inner_iters, svd_sweeps, svd_warm, svd_reorth, rank_A, oob_pixels;
+    int svt_qr;            // the SVT took the QR path
     double objective, lambda, kkt_residual;
     unsigned long long cyc_warp, cyc_svd, cyc_recon, cyc_elem, cyc_other;
 };
@@ -116,6 +117,7 @@ struct RaslProblem {
     double* col;           // nimg rows of RASL_COLW doubles
     double* tau;           // nimg x p, tau0 on entry, the result on exit
     int smem_svd, jsched;
+    int tall;              // the SVT takes the QR path (V, T, B_c and its buffers in shared memory)
     RaslResult* res;
 };
 
@@ -1121,6 +1123,13 @@ __host__ __device__ inline int staged_block(const Dims& d, size_t avail) {
 __host__ __device__ inline int default_schedule(int R, int C) {
     return ((R > 128 && C >= 64) ? 16 : 8) | JSCHED_BLOCK;
 }
+
+// Whether the SVT of an R x C matrix may take the QR path of svt_tall_qr (tall matrices: the
+// data matrices of RASL's image sets, one column per image).
+__host__ __device__ inline bool tall_qr_ok(const Dims& d) { return d.R >= 4 * d.C + 4 && d.C >= 2; }
+// Floats of the QR path's small buffers (buf.B): four C x C matrices at stride Cp and the
+// reflectors' heads and scales.
+__host__ __device__ inline size_t tall_small_floats(const Dims& d) { return ((size_t)4 * d.C + 2) * d.Cp; }
 
 // Schedule of a RASL set (long columns of m n pixels, one per image) whose size bucket the
 // autotuner has not timed: block-cyclic, 16 lanes per pair once the columns are 256 long

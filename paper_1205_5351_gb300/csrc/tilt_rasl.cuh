@@ -510,8 +510,9 @@ static __device__ InnerOut k_inner_rasl(const RaslProblem& pr, const Dims& d, co
         out.iters = k;
         // ---- a6 + a7: A' = S_{1/mu}(M), ||A' - A||^2 -> scal[7]
         t0 = clk();
+        // tall data matrices (the set's shared-memory plan has room for T) take the QR path
         const SvtStepOut so = svt_into<NCH, TCP>(dsvt, buf, L, haveV, sc->iscal[6] != 0, sc->fs[FS_IMU], A, nullptr,
-                                                 pr.jsched);
+                                                 pr.jsched, nullptr, nullptr, pr.tall != 0);
         const unsigned long long t1 = so.t_svd_end;
         if (threadIdx.x == 0) cyc->cyc_svd += t1 - t0;
         if (so.warm) out.warm++;
@@ -645,20 +646,29 @@ static __device__ void solve_rasl(const RaslProblem& pr, const SmemLayout& L, Ra
     const Params& prm = pr.prm;
     const int S = d.S;
     SvdBufs buf;
+    const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
+    // the QR path keeps V, T, B_c and its small buffers in shared memory (B is not formed)
+    const size_t nbB = pr.tall ? tall_small_floats(d) : nb;
     {
         float* sm = L.svd;
-        const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-        if (pr.smem_svd & 1) { buf.B = sm; sm += nb; } else { buf.B = pr.pl.Bg; }
-        if (pr.smem_svd & 2) { buf.V = sm; sm += nv; } else { buf.V = pr.pl.Vg; }
-        if (pr.smem_svd & 4) { buf.T = sm; sm += nb; } else { buf.T = pr.pl.Tg; }
-        if (pr.smem_svd & 8) { buf.Z = sm; sm += (size_t)d.C * d.Cp; } else { buf.Z = pr.pl.Zg; }
+        if (pr.tall) {
+            buf.V = sm; sm += nv;
+            buf.T = sm; sm += nb;
+            buf.Z = sm; sm += (size_t)d.C * d.Cp;
+            buf.B = sm; sm += nbB;
+        } else {
+            if (pr.smem_svd & 1) { buf.B = sm; sm += nb; } else { buf.B = pr.pl.Bg; }
+            if (pr.smem_svd & 2) { buf.V = sm; sm += nv; } else { buf.V = pr.pl.Vg; }
+            if (pr.smem_svd & 4) { buf.T = sm; sm += nb; } else { buf.T = pr.pl.Tg; }
+            if (pr.smem_svd & 8) { buf.Z = sm; sm += (size_t)d.C * d.Cp; } else { buf.Z = pr.pl.Zg; }
+        }
         buf.stage = reinterpret_cast<unsigned char*>(sm);
         buf.nbuf = 0;
         buf.tc = false;
     }
     {
-        const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
-        for (size_t e = threadIdx.x; e < nb; e += NT) { buf.B[e] = 0.f; buf.T[e] = 0.f; }
+        for (size_t e = threadIdx.x; e < nb; e += NT) buf.T[e] = 0.f;
+        for (size_t e = threadIdx.x; e < nbB; e += NT) buf.B[e] = 0.f;
         for (size_t e = threadIdx.x; e < nv; e += NT) buf.V[e] = 0.f;
     }
     const double lam = prm.lam > 0.0 ? prm.lam : 1.0 / sqrt((double)max(pr.m * pr.n, N));
@@ -763,6 +773,7 @@ static __device__ void solve_rasl(const RaslProblem& pr, const SmemLayout& L, Ra
         res.svd_warm = warm;
         res.svd_reorth = reorth;
         res.oob_pixels = sc->iscal[0];
+        res.svt_qr = pr.tall;
         res.kkt_residual = c1;
     }
     __syncthreads();

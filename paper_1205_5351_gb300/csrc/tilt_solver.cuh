@@ -9,7 +9,7 @@ namespace tilt {
 
 // Float scalars of one inner iteration, computed once by thread 0 in FP64 and read by all
 // threads from shared memory (Scratch::fs).
-enum { FS_IMU = 0, FS_THR = 1, FS_MU = 2, FS_IMUN = 3, FS_CC = 8 };
+enum { FS_IMU = 0, FS_THR = 1, FS_MU = 2, FS_IMUN = 3, FS_QRN = 4, FS_CC = 8 };
 // Loop control word (Scratch::iscal[5]) set by thread 0 at the end of an iteration.
 enum { LOOP_GO = 0, LOOP_CONVERGED = 1, LOOP_BAD = 2, LOOP_CANCELLED = 3 };
 
@@ -65,6 +65,267 @@ static __device__ void svt_select_factors(const Dims& d, CayBufs cb, float eps, 
     svt_select(C, eps, sigma, w, kept, sc);
 }
 
+// Singular value thresholding of a tall M (in buf.T, tall_qr_ok) through its QR factorisation:
+//   M = Q R_c by Householder reflectors H_j = I - beta_j v_j v_j^T, in place: R_c on and above
+//   the diagonal of T's top C x C block, v_j below it (v_j's head in vhead); then the
+//   one-sided Jacobi of the C x C matrix B_c = R_c V (warm from V, else B_c = R_c, V = I),
+//   whose columns then hold U_c Sigma.  With B = Q B_c the left-factor SVT of svt_into becomes
+//   S_eps(M) = Q [X_c; 0],   X_c = sum_kept (w_k / sigma_k^2) b_k (R_c^T b_k)^T   (b_k: B_c's),
+//   and Q = H_0 ... H_{C-1} = I - Vh Th Vh^T in the compact WY form (Schreiber and Van Loan,
+//   1989: Th upper triangular, Th_jj = beta_j, Th[0:j, j] = -beta_j Th[0:j, 0:j] Vh[:, 0:j]^T v_j),
+//   so A' = [X_c; 0] - Vh (Th (Vh_top^T X_c)) is one R x C x C product whose epilogue stores
+//   A (||A' - A||^2 in scal[7], J^T A' in ja[] when d.p > 0).  The sweeps' dot products run over
+//   C rows instead of R.  Buffers: B_c in buf.Z (C x C, stride Cp); buf.B holds
+//   tall_small_floats(d).  T is overwritten.  All threads.
+template <int NCH>
+static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const SmemLayout& L, bool& haveV, bool gate_ok,
+                                         float eps, float* __restrict__ A, const float* __restrict__ J) {
+    Scratch* sc = L.sc;
+    const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* T = buf.T;
+    float* Bc = buf.Z;                        // C x C at stride Cp
+    float* S0 = buf.B;                        // the SVT coefficients, then W1 = Vh_top^T X_c
+    float* Xc = S0 + (size_t)C * Cp;
+    float* S2 = Xc + (size_t)C * Cp;          // Vh^T Vh, then W2 = Th W1 (row-major: S2[a Cp + c])
+    float* Th = S2 + (size_t)C * Cp;
+    float* vhead = Th + (size_t)C * Cp;
+    float* beta = vhead + Cp;
+    SvtStepOut so;
+    so.sweeps = 0;
+    so.warm = false;
+    so.tc_timeout = false;
+    so.reorth = false;
+    so.cayley = false;
+    const bool warm = haveV && gate_ok;
+    if (warm && v_drift(buf.V, ldv, C, sc) > 1e-4f) {
+        v_reorth_fp64(buf.V, ldv, C, sc);
+        so.reorth = true;
+    }
+    // ---- Householder QR of T: H_j maps x = T[j .., j] to alpha e_1, alpha = -sign(x_0) ||x||,
+    // with v = (x_0 - alpha, x_1, ...) and beta = 1 / (||x||^2 + |x_0| ||x||)
+    float* n2s = &sc->fs[FS_QRN];             // ||T[j .., j]||^2 of the next column
+    if (warp == 0) {
+        float s2 = 0.f;
+        for (int i = lane; i < R; i += 32) s2 = fmaf(T[i], T[i], s2);
+        s2 = warp_sum(s2);
+        if (lane == 0) *n2s = s2;
+    }
+    __syncthreads();
+    for (int j = 0; j < C; ++j) {
+        float* tj = T + (size_t)j * ldb;
+        if (threadIdx.x == 0) {
+            const float x0 = tj[j], nrm2 = *n2s, nrm = sqrtf(nrm2);
+            const float alpha = nrm > 0.f ? (x0 >= 0.f ? -nrm : nrm) : 0.f;
+            vhead[j] = x0 - alpha;
+            beta[j] = nrm > 0.f ? 1.f / (nrm2 + fabsf(x0) * nrm) : 0.f;
+            tj[j] = alpha;
+        }
+        __syncthreads();
+        const float v0 = vhead[j], bj = beta[j];
+        for (int k = j + 1 + warp; k < C; k += NW) {
+            float* tk = T + (size_t)k * ldb;
+            const float tkj = tk[j];              // read by every lane before lane 0 rewrites it
+            float w = 0.f, w1 = 0.f;
+            int i = j + 1 + lane;
+#pragma unroll 2
+            for (; i + 32 < R; i += 64) {
+                w = fmaf(tj[i], tk[i], w);
+                w1 = fmaf(tj[i + 32], tk[i + 32], w1);
+            }
+            if (i < R) w = fmaf(tj[i], tk[i], w);
+            w = warp_sum(w + w1) + v0 * tkj;
+            const float f = bj * w;
+            if (lane == 0) tk[j] = tkj - f * v0;
+            float s2 = 0.f;
+#pragma unroll 4
+            for (int i2 = j + 1 + lane; i2 < R; i2 += 32) {
+                const float t = fmaf(-f, tj[i2], tk[i2]);
+                tk[i2] = t;
+                s2 = fmaf(t, t, s2);
+            }
+            if (k == j + 1) {
+                s2 = warp_sum(s2);
+                if (lane == 0) *n2s = s2;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- B_c = R_c V (warm) or R_c (cold, V = I); the SVD of B_c
+    for (int e = threadIdx.x; e < C * Cp; e += NT) {
+        const int c = e / Cp, i = e - c * Cp;
+        float v = 0.f;
+        if (i < C) {
+            if (warm) {
+                for (int k = i; k < C; ++k) v = fmaf(T[(size_t)k * ldb + i], buf.V[(size_t)c * ldv + k], v);
+            } else {
+                v = i <= c ? T[(size_t)c * ldb + i] : 0.f;
+            }
+        }
+        Bc[e] = v;
+    }
+    if (!warm) set_identity(buf.V, ldv, Cp);
+    __syncthreads();
+    so.warm = warm;
+    const int js = default_schedule(C, C);
+    so.sweeps = k2_jacobi<NCH>(Bc, Cp, buf.V, ldv, C, C, jacobi_tol(C), warm ? 30 : 40, sc->flag, jsched_width(js),
+                               jsched_order(js));
+    haveV = true;
+    svt_weights(Bc, Cp, C, C, eps, L.sigma, L.w, L.kept, sc);
+    so.t_svd_end = clk();
+    // ---- X_c = sum_kept (w_k / sigma_k^2) b_k (R_c^T b_k)^T
+    const int nk = sc->iscal[1];
+    for (int e = threadIdx.x; e < nk * C; e += NT) {
+        const int q = e / C, c = e - q * C;
+        const int k = L.kept[q];
+        const float* bk = Bc + (size_t)k * Cp;
+        const float* rc = T + (size_t)c * ldb;
+        float z = 0.f;
+        for (int i = 0; i <= c; ++i) z = fmaf(bk[i], rc[i], z);
+        const float sg = L.sigma[k];
+        S0[(size_t)q * Cp + c] = z * (L.w[k] / (sg * sg));
+    }
+    // Vh^T Vh by 4 x 4 tiles (upper block triangle), one warp per tile, lanes on consecutive rows
+    // (Vh[i, a] = T[i, a] below the diagonal, vhead[a] on it, 0 above)
+    {
+        const int ntc = Cp >> 2;
+        for (int t = warp; t < ntc * ntc; t += NW) {
+            const int ta = t / ntc, tb = t - ta * ntc;
+            if (ta > tb) continue;
+            const int a0 = 4 * ta, b0 = 4 * tb;
+            float g[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) g[x][y] = 0.f;
+            for (int i = a0 + lane; i < R; i += 32) {
+                float va[4], vb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int a = a0 + u, b = b0 + u;
+                    va[u] = a < C ? (i > a ? T[(size_t)a * ldb + i] : (i == a ? vhead[a] : 0.f)) : 0.f;
+                    vb[u] = b < C ? (i > b ? T[(size_t)b * ldb + i] : (i == b ? vhead[b] : 0.f)) : 0.f;
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) g[x][y] = fmaf(va[x], vb[y], g[x][y]);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) g[x][y] = warp_sum(g[x][y]);
+            if (lane == 0)
+                for (int x = 0; x < 4; ++x)
+                    for (int y = 0; y < 4; ++y) {
+                        const int a = a0 + x, b = b0 + y;
+                        if (a < b && b < C) S2[(size_t)b * Cp + a] = g[x][y];
+                    }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < C * C; e += NT) {
+        const int c = e / C, i = e - c * C;
+        float x = 0.f;
+        for (int q = 0; q < nk; ++q) x = fmaf(Bc[(size_t)L.kept[q] * Cp + i], S0[(size_t)q * Cp + c], x);
+        Xc[(size_t)c * Cp + i] = x;
+    }
+    // Th by its column recurrence (one warp)
+    if (warp == 0) {
+        for (int j = 0; j < C; ++j) {
+            for (int i = lane; i < j; i += 32) {
+                float t = 0.f;
+                for (int k = i; k < j; ++k) t = fmaf(Th[(size_t)k * Cp + i], S2[(size_t)j * Cp + k], t);
+                Th[(size_t)j * Cp + i] = -beta[j] * t;
+            }
+            if (lane == 0) Th[(size_t)j * Cp + j] = beta[j];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // W1 = Vh_top^T X_c (into S0), then W2 = Th W1 (into S2, row-major)
+    for (int e = threadIdx.x; e < C * C; e += NT) {
+        const int c = e / C, a = e - c * C;
+        const float* xc = Xc + (size_t)c * Cp;
+        const float* ta = T + (size_t)a * ldb;
+        float w = vhead[a] * xc[a];
+        for (int i = a + 1; i < C; ++i) w = fmaf(ta[i], xc[i], w);
+        S0[(size_t)c * Cp + a] = w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < C * Cp; e += NT) {
+        const int a = e / Cp, c = e - a * Cp;
+        float w = 0.f;
+        if (c < C)
+            for (int k = a; k < C; ++k) w = fmaf(Th[(size_t)k * Cp + a], S0[(size_t)c * Cp + k], w);
+        S2[(size_t)a * Cp + c] = w;
+    }
+    __syncthreads();
+    // ---- A' = [X_c; 0] - Vh W2: one row of four columns per item, consecutive threads on
+    // consecutive rows (coalesced accesses of A; W2's rows are broadcast float4 reads).  A
+    // thread takes its items four at a time and loads their old values of A before any of
+    // their stores, so the loads of a batch are in flight together (a load of A that follows
+    // a store to A cannot be moved ahead of it)
+    float acc[1 + PMAX];
+#pragma unroll
+    for (int k2 = 0; k2 < 1 + PMAX; ++k2) acc[k2] = 0.f;
+    const int nc4 = Cp >> 2;
+    const int items = R * nc4;
+    constexpr int NB = 4;
+    for (int base = threadIdx.x; base < items; base += NB * NT) {
+        float aold[NB][4];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int idx = base + b * NT;
+            const int c4 = idx / R, i = idx - c4 * R;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * c4 + u;
+                aold[b][u] = (idx < items && c < C) ? A[(size_t)c * R + i] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int idx = base + b * NT;
+            if (idx >= items) break;
+            const int c4 = idx / R, i = idx - c4 * R;
+            const int c0 = 4 * c4;
+            float4 sv = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int amax = min(i, C - 1);
+            for (int a = 0; a <= amax; ++a) {
+                const float vh = a == i ? vhead[a] : T[(size_t)a * ldb + i];
+                const float4 w2 = *reinterpret_cast<const float4*>(S2 + (size_t)a * Cp + c0);
+                sv.x = fmaf(vh, w2.x, sv.x);
+                sv.y = fmaf(vh, w2.y, sv.y);
+                sv.z = fmaf(vh, w2.z, sv.z);
+                sv.w = fmaf(vh, w2.w, sv.w);
+            }
+            const float su[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u;
+                if (c < C) {
+                    const float sa = (i < C ? Xc[(size_t)c * Cp + i] : 0.f) - su[u];
+                    const int e = c * R + i;
+                    const float da = sa - aold[b][u];
+                    acc[0] = fmaf(da, da, acc[0]);
+                    A[e] = sa;
+#pragma unroll
+                    for (int k2 = 0; k2 < PMAX; ++k2)
+                        if (k2 < p) acc[1 + k2] = fmaf(J[(size_t)k2 * S + e], sa, acc[1 + k2]);
+                }
+            }
+        }
+    }
+    block_sum_f<1 + PMAX>(acc, sc->red);
+    if (threadIdx.x == 0) {
+        sc->scal[7] = block_total(sc->red, 0);
+        for (int k2 = 0; k2 < p; ++k2) sc->ja[k2] = block_total(sc->red, 1 + k2);
+    }
+    __syncthreads();
+    return so;
+}
+
 // Singular value thresholding of the iteration's M (in buf.T): the one-sided Jacobi SVD,
 // warm-started from V when one exists, the gate allows and V has not drifted (a6), then
 // A' = S_eps(M) by the left-factor reconstruction (a7), stored into A with ||A' - A||^2 in
@@ -78,7 +339,7 @@ static __device__ void svt_select_factors(const Dims& d, CayBufs cb, float eps, 
 template <int NCH, bool TCP>
 static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& buf, const SmemLayout& L, bool& haveV, bool gate_ok,
                                       float eps, float* __restrict__ A, const float* __restrict__ J, int jsched,
-                                      float* cay = nullptr, bool* haveUS = nullptr) {
+                                      float* cay = nullptr, bool* haveUS = nullptr, bool tall = false) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, C = d.C, ldb = d.ldb, ldv = d.ldv, Cp = d.Cp;
     SvtStepOut so;
@@ -127,6 +388,7 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
             return so;
         }
     }
+    if (tall && tall_qr_ok(d)) return svt_tall_qr<NCH>(d, buf, L, haveV, gate_ok, eps, A, J);
     const bool warm = haveV && gate_ok;
     // FP32 rotations let V drift from orthogonal over many warm starts; past 1e-4 in a column
     // norm it is re-orthonormalised in FP64 and the warm start goes ahead

@@ -72,13 +72,15 @@ class Result(ctypes.Structure):
 class RaslResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
                 ("svd_sweeps", ctypes.c_int), ("svd_warm", ctypes.c_int), ("svd_reorth", ctypes.c_int),
-                ("rank", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("objective", ctypes.c_double),
+                ("rank", ctypes.c_int), ("oob_pixels", ctypes.c_int), ("svt_qr", ctypes.c_int),
+                ("objective", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("kkt_residual", ctypes.c_double), ("cycles", ctypes.c_uint64 * 5)]
 
     def to_dict(self) -> dict:
         return dict(status=self.status, outer_iters=self.outer_iters, inner_iters=self.inner_iters,
                     svd_sweeps=self.svd_sweeps, svd_warm=self.svd_warm, svd_reorth=self.svd_reorth,
-                    rank=self.rank, oob=self.oob_pixels, objective=self.objective, lam=self.lambda_,
+                    rank=self.rank, oob=self.oob_pixels, svt_qr=self.svt_qr, objective=self.objective,
+                    lam=self.lambda_,
                     kkt=self.kkt_residual, phase_cycles=list(self.cycles))
 
 

@@ -46,9 +46,12 @@ def _run(T, ctx, sets, prm, planes=True):
     return ctx.rasl(imgs, s0.m, s0.n, tau0, s0.ttype, prm, planes=planes)
 
 
-# (nimg, m, n, ttype): small windows with B, V, T in shared memory; 33 images (three columns
-# for some warps); 40 images of 48 x 48 (R = 2304: B in device memory, staged Jacobi sweeps)
+# (nimg, m, n, ttype): small windows (the SVT through the QR factorisation of M, whose
+# buffers fit in shared memory); 33 images (three columns for some warps); 40 images of
+# 48 x 48 (R = 2304: M too large for shared memory, so the one-sided Jacobi on M itself with
+# B in device memory and staged sweeps)
 CASES = [(6, 12, 14, 6), (9, 16, 11, 8), (33, 20, 20, 6), (40, 48, 48, 6)]
+QR_PATH = {(6, 12, 14): 1, (9, 16, 11): 1, (33, 20, 20): 1, (40, 48, 48): 0}
 
 
 @pytest.mark.parametrize("nimg,m,n,ttype", CASES)
@@ -63,6 +66,7 @@ def test_rasl_one_iteration_parity(T, ctx, nimg, m, n, ttype):
         ref = O.rasl(s.imgs.astype(np.float64), s.tau0, ttype, m, n, O.Params(max_outer=1, max_inner=1))
         r = out["results"][k]
         assert (r["status"], r["outer_iters"], r["inner_iters"]) == (2, 1, 1), r
+        assert r["svt_qr"] == QR_PATH[(nimg, m, n)], r
         # the step in image space, J dtau (J the stacked Jacobian at tau0): independent of how
         # the transform is parametrised
         Jb = O.rasl_stacked_jacobian(O.rasl_warp(s.imgs.astype(np.float64), s.tau0, ttype, m, n)[1])
