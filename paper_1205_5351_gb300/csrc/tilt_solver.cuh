@@ -173,17 +173,15 @@ static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const Smem
     haveV = true;
     svt_weights(Bc, Cp, C, C, eps, L.sigma, L.w, L.kept, sc);
     so.t_svd_end = clk();
-    // ---- X_c = sum_kept (w_k / sigma_k^2) b_k (R_c^T b_k)^T
+    // ---- X_c = sum_kept (w_k / sigma_k^2) b_k (R_c^T b_k)^T and the compact WY form.  The
+    // small products run with consecutive threads on consecutive columns of row-major operands
+    // (R_c^T, X_c, W1, W2 are stored by rows), so that no shared-memory access of a warp strides
+    // across one bank
     const int nk = sc->iscal[1];
-    for (int e = threadIdx.x; e < nk * C; e += NT) {
-        const int q = e / C, c = e - q * C;
-        const int k = L.kept[q];
-        const float* bk = Bc + (size_t)k * Cp;
-        const float* rc = T + (size_t)c * ldb;
-        float z = 0.f;
-        for (int i = 0; i <= c; ++i) z = fmaf(bk[i], rc[i], z);
-        const float sg = L.sigma[k];
-        S0[(size_t)q * Cp + c] = z * (L.w[k] / (sg * sg));
+    float* Rt = Th;                            // R_c by rows until Th is formed
+    for (int e = threadIdx.x; e < C * C; e += NT) {
+        const int i = e / C, c = e - i * C;
+        Rt[(size_t)i * Cp + c] = i <= c ? T[(size_t)c * ldb + i] : 0.f;
     }
     // Vh^T Vh by 4 x 4 tiles (upper block triangle), one warp per tile, lanes on consecutive rows
     // (Vh[i, a] = T[i, a] below the diagonal, vhead[a] on it, 0 above)
@@ -224,13 +222,25 @@ static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const Smem
         }
     }
     __syncthreads();
+    // the coefficients Z (nk x C, by rows): (w_k / sigma_k^2) (R_c^T b_k)^T
+    for (int e = threadIdx.x; e < nk * C; e += NT) {
+        const int q = e / C, c = e - q * C;
+        const int k = L.kept[q];
+        const float* bk = Bc + (size_t)k * Cp;
+        float z = 0.f;
+        for (int i = 0; i <= c; ++i) z = fmaf(bk[i], Rt[(size_t)i * Cp + c], z);
+        const float sg = L.sigma[k];
+        S0[(size_t)q * Cp + c] = z * (L.w[k] / (sg * sg));
+    }
+    __syncthreads();
+    // X_c = B_c,K Z (by rows)
     for (int e = threadIdx.x; e < C * C; e += NT) {
-        const int c = e / C, i = e - c * C;
+        const int i = e / C, c = e - i * C;
         float x = 0.f;
         for (int q = 0; q < nk; ++q) x = fmaf(Bc[(size_t)L.kept[q] * Cp + i], S0[(size_t)q * Cp + c], x);
-        Xc[(size_t)c * Cp + i] = x;
+        Xc[(size_t)i * Cp + c] = x;
     }
-    // Th by its column recurrence (one warp)
+    // Th by its column recurrence (one warp; R_c^T is no longer needed)
     if (warp == 0) {
         for (int j = 0; j < C; ++j) {
             for (int i = lane; i < j; i += 32) {
@@ -243,21 +253,20 @@ static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const Smem
         }
     }
     __syncthreads();
-    // W1 = Vh_top^T X_c (into S0), then W2 = Th W1 (into S2, row-major)
+    // W1 = Vh_top^T X_c (into S0, by rows), then W2 = Th W1 (into S2, by rows)
     for (int e = threadIdx.x; e < C * C; e += NT) {
-        const int c = e / C, a = e - c * C;
-        const float* xc = Xc + (size_t)c * Cp;
+        const int a = e / C, c = e - a * C;
         const float* ta = T + (size_t)a * ldb;
-        float w = vhead[a] * xc[a];
-        for (int i = a + 1; i < C; ++i) w = fmaf(ta[i], xc[i], w);
-        S0[(size_t)c * Cp + a] = w;
+        float w = vhead[a] * Xc[(size_t)a * Cp + c];
+        for (int i = a + 1; i < C; ++i) w = fmaf(ta[i], Xc[(size_t)i * Cp + c], w);
+        S0[(size_t)a * Cp + c] = w;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < C * Cp; e += NT) {
         const int a = e / Cp, c = e - a * Cp;
         float w = 0.f;
         if (c < C)
-            for (int k = a; k < C; ++k) w = fmaf(Th[(size_t)k * Cp + a], S0[(size_t)c * Cp + k], w);
+            for (int k = a; k < C; ++k) w = fmaf(Th[(size_t)k * Cp + a], S0[(size_t)k * Cp + c], w);
         S2[(size_t)a * Cp + c] = w;
     }
     __syncthreads();
@@ -305,7 +314,7 @@ static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const Smem
             for (int u = 0; u < 4; ++u) {
                 const int c = c0 + u;
                 if (c < C) {
-                    const float sa = (i < C ? Xc[(size_t)c * Cp + i] : 0.f) - su[u];
+                    const float sa = (i < C ? Xc[(size_t)i * Cp + c] : 0.f) - su[u];
                     const int e = c * R + i;
                     const float da = sa - aold[b][u];
                     acc[0] = fmaf(da, da, acc[0]);
