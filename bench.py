@@ -70,9 +70,9 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partition
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
 # sources they were taken on: when the SHA-256 of csrc/ and include/ (comments removed)
 # differs, traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "d8650171d154fca5840c85635c6705bd9193733f2acc4b64f3325803bdd3b536",
-               "bytes": {"affine/1024/0": 5576398848 + 6401972480,
-                         "affine/1024/1": 6565076736 + 6313976576}}
+NCU_TRAFFIC = {"sources_sha256": "d252326bc15fe2f8cafd94e8e46e5cea0117d2711d79994c803104525e82ba1e",
+               "bytes": {"affine/1024/0": 6373596672 + 7015059968,
+                         "affine/1024/1": 6472209408 + 6242443264}}
 
 
 def strip_c_comments(src: str) -> str:
