@@ -98,7 +98,11 @@ def _svd(M):
             if dt < best_t:
                 best, best_t = drv, dt
         _DRIVER[key] = best
-    return torch.linalg.svd(M, full_matrices=False, driver=_DRIVER[key])
+    try:
+        return torch.linalg.svd(M, full_matrices=False, driver=_DRIVER[key])
+    except RuntimeError:
+        # the Jacobi or approximate driver did not converge on this matrix: QR iteration
+        return torch.linalg.svd(M, full_matrices=False, driver="gesvd")
 
 
 def tilt_plain(img, tau0, ttype, m, n, eps1=1e-5, eps2=0.1, rho0=1.5, mu_max=1e10, max_inner=500,
