@@ -4,7 +4,9 @@
 One step = the whole hot path (Algorithm 1: warp, normalise, Jacobian, Gram/Q, inner
 LADMAP loop with Jacobi SVT, dtau, tau update, all outer steps) over one batch of 1024
 affine patches with sides uniform in 40..120 (synthetic, seeded), submitted through the
-C ABI as grouped launches and polled to completion.
+C ABI as grouped launches and polled to completion.  The K timed steps run back to back with
+at most two batches in flight (what a caller feeding a stream of batches sees); one batch
+alone is timed beside them for the latency and per-launch figures.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -68,9 +70,9 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partition
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grouped launch of the solver
 # kernel, by workload and launch class, from one ncu capture of the full-size workload (the
 # command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
-# sources they were taken on: when the SHA-256 of csrc/ and include/ (comments removed)
-# differs, traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "d252326bc15fe2f8cafd94e8e46e5cea0117d2711d79994c803104525e82ba1e",
+# sources they were taken on: when the SHA-256 of SOLVER_SOURCES (comments removed) differs,
+# traffic is null.
+NCU_TRAFFIC = {"sources_sha256": "0a2fedb433a1e9121a9dbce75cd6a75d6906df8c5b17e18a03b01676ac311dfd",
                "bytes": {"affine/1024/0": 6373596672 + 7015059968,
                          "affine/1024/1": 6472209408 + 6242443264}}
 
@@ -100,17 +102,24 @@ def strip_c_comments(src: str) -> str:
     return " ".join("".join(out).split())
 
 
+# The sources the solver kernel is compiled from (its translation units and the headers they
+# include): the recorded counters describe the kernel these produce.
+SOLVER_SOURCES = ("tilt_device.cuh", "tilt_solver.cuh", "tilt_tc.cuh", "tilt_cayley.cuh", "tilt_launch.h",
+                  "tilt_kernels.cu", "tilt_kernels_tc.cu")
+
+
 def kernel_sources_sha256() -> str:
-    """SHA-256 of the library's CUDA/C++ sources with comments and layout removed: a change
-    of code invalidates recorded counters, an edit of comments does not."""
+    """SHA-256 of the solver kernel's sources with comments and layout removed: a change of
+    their code invalidates recorded counters, an edit of comments does not (nor does a change
+    of host-only code such as the context's planning and streams)."""
     import hashlib
     h = hashlib.sha256()
-    dirs = [os.path.join(ROOT, "paper_1205_5351_gb300", "csrc"), os.path.join(ROOT, "include")]
-    for d in dirs:
-        for f in sorted(os.listdir(d)):
-            if f.endswith((".cu", ".cuh", ".h")):
-                h.update(f.encode())
-                h.update(strip_c_comments(open(os.path.join(d, f)).read()).encode())
+    d = os.path.join(ROOT, "paper_1205_5351_gb300", "csrc")
+    for f in SOLVER_SOURCES:
+        path = os.path.join(d, f)
+        if os.path.exists(path):
+            h.update(f.encode())
+            h.update(strip_c_comments(open(path).read()).encode())
     return h.hexdigest()
 
 
@@ -320,9 +329,8 @@ def run_ours(args, rank, world, local_rank, dist):
         over = {**over, "svd_ws": 1, "eps_svd": args.eps_svd}
     params = tilt.default_params(**{**wl_params, **over})
 
-    def step(items, on_device, planes):
-        t_sub = time.perf_counter()
-        tickets = ctx.submit_batch(items, params, on_device=on_device)
+    def wait(tickets, planes, t_sub=None):
+        """Poll the tickets to completion; results and completion times (s after t_sub)."""
         pending = dict(enumerate(tickets))
         res = [None] * len(tickets)
         done_at = [0.0] * len(tickets)
@@ -332,9 +340,30 @@ def run_ours(args, rank, world, local_rank, dist):
                 r = ctx.poll(pending[q], with_planes=planes, m=p.m, n=p.n)
                 if r is not None:
                     res[q] = r
-                    done_at[q] = time.perf_counter() - t_sub
+                    if t_sub is not None:
+                        done_at[q] = time.perf_counter() - t_sub
                     del pending[q]
         return res, done_at
+
+    def step(items, on_device, planes):
+        t_sub = time.perf_counter()
+        tickets = ctx.submit_batch(items, params, on_device=on_device)
+        return wait(tickets, planes, t_sub)
+
+    def pipelined(items, on_device, planes, k_steps):
+        """k_steps batches back to back, at most two in flight: batch k + 1 is submitted before
+        batch k is waited for, so its launches take the SMs that batch k frees while batch k's
+        longest solves run (the context alternates stream sets between batches)."""
+        prev = None
+        last = None
+        for _ in range(k_steps):
+            cur = ctx.submit_batch(items, params, on_device=on_device)
+            if prev is not None:
+                wait(prev, planes)
+            prev = cur
+        if prev is not None:
+            last, _ = wait(prev, planes)
+        return last
 
     def barrier():
         torch.cuda.synchronize()
@@ -349,40 +378,52 @@ def run_ours(args, rank, world, local_rank, dist):
     tune_s = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         step(items_dev, True, False)
-    # ---- timed: device-resident inputs
+    # ---- timed (the value): K steps pipelined, device-resident inputs.  The inputs exceed L2
+    # (the images alone are larger than it, and every step writes its planes), so L2 is flushed
+    # once before the region, not between steps that overlap
     clocks = ClockSampler(local_rank)
     clocks.start()
-    times, kernel_ms, results, lat = [], [], None, []
     launches0 = ctx.launches
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        barrier()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        results, done_at = step(items_dev, True, False)
-        ev1.record()
-        torch.cuda.synchronize()
-        times.append(ev0.elapsed_time(ev1))
-        kernel_ms.append(ctx.batch_kernel_ms())
-        lat += [1e3 * t for t in done_at]
+    flush.fill_(1.0)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    pipelined(items_dev, True, False, args.steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_pipe = ev0.elapsed_time(ev1)
     launches = ctx.launches - launches0
     clk = clocks.stop()
-    # ---- timed: end to end through the C ABI with host buffers (pinned images in, A and E out)
-    e2e_times = []
-    h2d = sum(p.img.nbytes for p in patches)
-    d2h = sum(2 * 4 * p.m * p.n for p in patches)
-    for _ in range(max(1, args.steps)):
+    # ---- isolated steps (flush before each): latency of every patch from the batch's submit,
+    # per-launch kernel durations for the roofline, and the results for the parity sample
+    times, kernel_ms, results, lat = [], [], None, []
+    for _ in range(max(1, min(args.steps, 3))):
         flush.fill_(1.0)
         barrier()
-        t0 = time.perf_counter()
-        step(items_host, False, True)
-        e2e_times.append(1e3 * (time.perf_counter() - t0))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        results, done_at = step(items_dev, True, False)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kernel_ms.append(ctx.batch_kernel_ms())
+        lat += [1e3 * t for t in done_at]
+    # ---- timed: end to end through the C ABI with host buffers (pinned images in, A and E
+    # out), pipelined as the value
+    h2d = sum(p.img.nbytes for p in patches)
+    d2h = sum(2 * 4 * p.m * p.n for p in patches)
+    flush.fill_(1.0)
+    barrier()
+    t0 = time.perf_counter()
+    pipelined(items_host, False, True, max(1, args.steps))
+    e2e_ms = 1e3 * (time.perf_counter() - t0)
 
     from paper_1205_5351_gb300 import multigpu
-    ms = statistics.mean(times)
-    # max over ranks of the timed regions (each rank solved its own batch: weak scaling)
-    tot = multigpu.max_over_ranks([max(times), max(e2e_times)], dist, dev)
+    ms = t_pipe / max(1, args.steps)
+    # max over ranks of the timed regions (each rank solved its own batches: weak scaling)
+    tot = multigpu.max_over_ranks([t_pipe, e2e_ms, max(times)], dist, dev)
     n_total = args.patches * world
+    k_steps = max(1, args.steps)
     inner = sum(r["inner_iters"] for r in results)
     out = None
     if rank == 0:
@@ -438,10 +479,16 @@ def run_ours(args, rank, world, local_rank, dist):
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": desc, "patches_per_gpu": len(patches), "p": patches[0].ttype,
-                       "l2": "512 MiB written before every step; inputs exceed L2"},
-            "ladmap_iters_per_s": inner * world / (max(times) * 1e-3),
+                       "l2": "inputs exceed L2 (images alone: %.0f MB; planes written every step); 512 MiB "
+                             "written before the timed region and before each isolated step" % (h2d / 1e6),
+                       "steps": "timed region: the K steps back to back, at most two batches in flight (a "
+                                "batch starts on the SMs the previous one frees while its longest solves "
+                                "run); every patch of every step solved"},
+            "isolated_step": {"ms": statistics.mean(times), "patches_per_s": n_total / (float(tot[2]) * 1e-3),
+                              "note": "one batch alone (L2 flushed before it), the slowest of up to 3"},
+            "ladmap_iters_per_s": inner * world * k_steps / (float(tot[0]) * 1e-3),
             "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99),
-                           "note": "submit of the batch to completion of each patch"},
+                           "note": "isolated steps: submit of the batch to completion of each patch"},
             "status_counts": {str(s): sum(1 for r in results if r["status"] == s)
                               for s in sorted({r["status"] for r in results})},
             "inner_iters_per_patch": inner / len(results),
@@ -461,7 +508,8 @@ def run_ours(args, rank, world, local_rank, dist):
                           "per_class": {str(c): t for c, t in zip(classes, per_class_ms)},
                           "patches_per_class": {str(c): sum(1 for r in results if r["launch_class"] == c)
                                                 for c in classes}},
-            "converged_patches_per_s": sum(1 for r in results if r["status"] == 0) * world / (max(times) * 1e-3),
+            "converged_patches_per_s": sum(1 for r in results if r["status"] == 0) * world * k_steps
+                                       / (float(tot[0]) * 1e-3),
             "phase_roofline": phase_roof,
             "slowest_patch": (lambda q: {"m": patches[q].m, "n": patches[q].n, "kind": patches[q].meta["kind"],
                                          "done_ms": lat[q], "outer": results[q]["outer_iters"],
@@ -477,16 +525,16 @@ def run_ours(args, rank, world, local_rank, dist):
                          "flops_per_launch": dom_flops,
                          "peak_source": "%d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz (median SM clock "
                                         "sampled during the timed steps): FP32 FMA issue rate" % (n_sms, mhz)},
-            "gpu_launches": launches,                 # solver launches inside the timed steps
-            "gpu_launches_per_step": launches // max(1, args.steps),
+            "gpu_launches": launches,                 # solver launches inside the timed region
+            "gpu_launches_per_step": launches // k_steps,
             "autotune_s": round(tune_s, 2),
             "autotune_schedules": {("gw%d%s" % (w & 255, "-block" if w >> 8 else "")): widths.count(w)
                                    for w in sorted(set(widths))},
             "clocks": clk,
-            "e2e": {"value": n_total / (float(tot[1]) * 1e-3), "unit": "patches/s",
+            "e2e": {"value": n_total * k_steps / (float(tot[1]) * 1e-3), "unit": "patches/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
-        value = n_total / (float(tot[0]) * 1e-3)
+        value = n_total * k_steps / (float(tot[0]) * 1e-3)
         if args.workload in ("convergence", "corruption"):
             from paper_1205_5351_gb300 import sweeps
             out["sweep"] = (sweeps.convergence_map if args.workload == "convergence"

@@ -168,7 +168,10 @@ typedef struct {
  * largest first, so that the block scheduler balances the load; a batch of at most one
  * problem per SM runs every problem one CTA per SM).  Same semantics as
  * count calls of tilt_submit; tickets_out[count] receives the tickets.  Either every
- * problem is admitted or none is (TILT_E_NOMEM / TILT_E_BUSY). */
+ * problem is admitted or none is (TILT_E_NOMEM / TILT_E_BUSY).  With the context's own
+ * streams, consecutive batches alternate between two sets of streams: a batch submitted while
+ * the previous one still runs starts on the SMs that batch frees (its longest solves finish
+ * alongside). */
 int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* problems, int is_device_ptr,
                       const tilt_params* params, uint64_t* tickets_out);
 

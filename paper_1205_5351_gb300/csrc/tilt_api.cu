@@ -139,7 +139,7 @@ struct tilt_ctx {
     int device = 0;
     int max_live = 0;
     size_t max_smem = 0;
-    cudaStream_t streams[4] = {};
+    cudaStream_t streams[6] = {};   // two sets of three (one per launch class), alternating by batch
     cudaStream_t copy_stream = nullptr;
     bool own_streams = true;        // false: streams[] and copy_stream are the caller's stream
     int next_stream = 0;
@@ -787,7 +787,10 @@ int tilt_submit_batch(tilt_ctx* ctx, int count, const tilt_problem* probs, int i
         t.t_submit = t0;
         ids[q] = ctx->next_ticket++;
     }
-    cudaStream_t st[3] = {ctx->streams[0], ctx->streams[1], ctx->streams[2]};
+    // consecutive batches take alternate stream sets, so that a batch's launches start on the
+    // SMs the previous batch frees while its longest solves still run
+    const int sset = 3 * (bid & 1);
+    cudaStream_t st[3] = {ctx->streams[sset], ctx->streams[sset + 1], ctx->streams[sset + 2]};
     for (int q = 0; q < count; ++q) {
         Ticket& t = ctx->tickets.emplace(ids[q], std::move(ts[q])).first->second;
         int rc = prepare(ctx, t, st[cls(q)]);

@@ -9,16 +9,19 @@ def test_strip_c_comments_keeps_code_and_literals():
 
 
 def test_comment_edits_keep_the_hash_and_code_edits_change_it(tmp_path, monkeypatch):
-    for d in ("paper_1205_5351_gb300/csrc", "include"):
-        (tmp_path / d).mkdir(parents=True)
-    f = tmp_path / "include" / "x.h"
+    (tmp_path / "paper_1205_5351_gb300" / "csrc").mkdir(parents=True)
+    f = tmp_path / "paper_1205_5351_gb300" / "csrc" / bench.SOLVER_SOURCES[0]
     f.write_text("int f(int a) { return a + 1; }  // one\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench.kernel_sources_sha256()
     f.write_text("/* a new\n   comment */\nint f(int a) {\n    return a + 1;   // two\n}\n")
     assert bench.kernel_sources_sha256() == h0
     f.write_text("int f(int a) { return a + 2; }\n")
-    assert bench.kernel_sources_sha256() != h0
+    h1 = bench.kernel_sources_sha256()
+    assert h1 != h0
+    # host-only sources are not part of it
+    (tmp_path / "paper_1205_5351_gb300" / "csrc" / "tilt_api.cu").write_text("int g() { return 3; }\n")
+    assert bench.kernel_sources_sha256() == h1
 
 
 def test_reference_arm_prints_the_contract_line():
