@@ -68,8 +68,9 @@ def make_patches(workload, count, first):
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partitions x 32)
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per grouped launch of the solver
-# kernel, by workload and launch class, from one ncu capture of the full-size workload (the
-# command is in profiles/solver_kernel_affine1024_dram.md).  They hold only for the kernel
+# kernel, by workload and launch class, from one ncu capture of the full-size workload (one
+# metric pass per launch over `bench.py --steps 1 --warmup 1`, the timed step's launches).
+# They hold only for the kernel
 # sources they were taken on: when the SHA-256 of SOLVER_SOURCES (comments removed) differs,
 # traffic is null.
 NCU_TRAFFIC = {"sources_sha256": "0a2fedb433a1e9121a9dbce75cd6a75d6906df8c5b17e18a03b01676ac311dfd",
