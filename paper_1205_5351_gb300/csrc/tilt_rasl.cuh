@@ -220,6 +220,22 @@ __device__ __forceinline__ void col_y_update(const float* __restrict__ A, const 
     }
 }
 
+// s + c += x y without rounding error of the product and of the sum beyond FP32's own: the
+// product's rounding error from an FMA and the sum's from Knuth's two-sum, carried in c (the
+// compensated dot product of Ogita, Rump and Oishi, 2005).  The per-lane sums of the set's
+// once-per-outer-step reductions run in FP32 this way, as accurate as FP64 sums of the same
+// FP32 data and several times cheaper on this part (FP64 issues at 1/64 of the FP32 rate).
+// (The _rn intrinsics keep the compiler from fusing a product into a neighbouring sum, which
+// would break the error terms.)
+__device__ __forceinline__ void dot2_add(float& s, float& c, float x, float y) {
+    const float prod = __fmul_rn(x, y);
+    const float perr = fmaf(x, y, -prod);
+    const float t = __fadd_rn(s, prod);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(prod, z)), perr));
+    s = t;
+}
+
 // Step 1 of Algorithm 1 for every image of the set: column c of D_hat is image c sampled at
 // tau_c over the window (pixel r = i n + j), divided by its Frobenius norm; column c of J_k
 // the derivative of that normalised column by tau_c[k] (the quotient rule, per column).  One
@@ -240,9 +256,10 @@ static __device__ void rasl_warp(const RaslProblem& pr, const Dims& d, float* __
         const float* img = pr.imgs + (size_t)c * pr.img_stride;
         float* Dc = Dhat + (size_t)c * R;
         float* Jc = J + (size_t)c * R;
-        double acc[2 + PMAX];
+        float fs[1 + PMAX], fc[1 + PMAX];     // ||D||^2, D . Jraw_k (compensated FP32)
 #pragma unroll
-        for (int k = 0; k < 2 + PMAX; ++k) acc[k] = 0.0;
+        for (int k = 0; k < 1 + PMAX; ++k) { fs[k] = 0.f; fc[k] = 0.f; }
+        int nout = 0;
         for (int r = lane; r < R; r += 32) {
             const int i = r / n, j = r - i * n;
             const double u = (double)j - hn, v = (double)i - hm;
@@ -250,18 +267,21 @@ static __device__ void rasl_warp(const RaslProblem& pr, const Dims& d, float* __
             bool inside;
             const float val = warp_sample(img, pr.ld, pr.H, pr.W, pr.ttype, tau, u, v, jr, inside);
             Dc[r] = val;
-            acc[0] += (double)val * (double)val;
-            acc[1] += inside ? 0.0 : 1.0;
+            dot2_add(fs[0], fc[0], val, val);
+            nout += inside ? 0 : 1;
 #pragma unroll
             for (int k = 0; k < PMAX; ++k) {
                 if (k < p) {
                     Jc[(size_t)k * S + r] = jr[k];
-                    acc[2 + k] += (double)val * (double)jr[k];
+                    dot2_add(fs[1 + k], fc[1 + k], val, jr[k]);
                 }
             }
         }
+        double acc[2 + PMAX];
+        acc[0] = warp_sum64((double)fs[0] + (double)fc[0]);
+        acc[1] = warp_sum64((double)nout);
 #pragma unroll
-        for (int k = 0; k < 2 + PMAX; ++k) acc[k] = warp_sum64(acc[k]);
+        for (int k = 0; k < PMAX; ++k) acc[2 + k] = warp_sum64((double)fs[1 + k] + (double)fc[1 + k]);
         const double s = sqrt(acc[0]);
         const float inv = (s > 0.0) ? (float)(1.0 / s) : 0.f;
         float a[PMAX];
@@ -315,23 +335,24 @@ static __device__ bool rasl_gram(const RaslProblem& pr, const Dims& d, const flo
         const float* Jc = J + (size_t)c * R;
 #pragma unroll 1
         for (int q0 = 0; q0 < NPROD; q0 += CH) {
-            double acc[CH];
+            float fs[CH], fc[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) acc[k] = 0.0;
+            for (int k = 0; k < CH; ++k) { fs[k] = 0.f; fc[k] = 0.f; }
             for (int r = lane; r < R; r += 32) {
-                const double dh = (double)Dc[r];
+                const float dh = Dc[r];
 #pragma unroll
                 for (int k = 0; k < CH; ++k) {
                     int a, b;
                     gram_index(q0 + k, a, b);
                     if (a >= p || b >= p) continue;
-                    const double va = a < 0 ? dh : (double)Jc[(size_t)a * S + r];
-                    const double vb = b < 0 ? dh : (double)Jc[(size_t)b * S + r];
-                    acc[k] += va * vb;
+                    const float va = a < 0 ? dh : Jc[(size_t)a * S + r];
+                    const float vb = b < 0 ? dh : Jc[(size_t)b * S + r];
+                    dot2_add(fs[k], fc[k], va, vb);
                 }
             }
+            double acc[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) acc[k] = warp_sum64(acc[k]);
+            for (int k = 0; k < CH; ++k) acc[k] = warp_sum64((double)fs[k] + (double)fc[k]);
             if (lane == 0)
                 for (int k = 0; k < CH; ++k) row[RC_G + q0 + k] = acc[k];   // staging
         }
