@@ -73,9 +73,9 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partition
 # They hold only for the kernel
 # sources they were taken on: when the SHA-256 of SOLVER_SOURCES (comments removed) differs,
 # traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "0a2fedb433a1e9121a9dbce75cd6a75d6906df8c5b17e18a03b01676ac311dfd",
-               "bytes": {"affine/1024/0": 6373596672 + 7015059968,
-                         "affine/1024/1": 6472209408 + 6242443264}}
+NCU_TRAFFIC = {"sources_sha256": "1f53afb690d3e8e408659aec4f521a42f1b6c7af2828e79d0a89fcf7ae3f25bc",
+               "bytes": {"affine/1024/0": 2997433600 + 3390507008,
+                         "affine/1024/1": 2403687680 + 2710898688}}
 
 
 def strip_c_comments(src: str) -> str:

@@ -1162,12 +1162,11 @@ int tilt_inner(tilt_ctx* ctx, const float* Dhat_dev, const float* J_dev, int m, 
     const size_t nb = (size_t)d.ldb * d.Cp, nv = (size_t)d.ldv * d.Cp;
     const size_t S4 = ((size_t)d.S + 63) & ~(size_t)63, nz = ((size_t)d.C * d.Cp + 63) & ~(size_t)63;
     const size_t ncay = a.prm.svd_ws == 1 ? ((cayley_floats(d) + 63) & ~(size_t)63) : 0;
-    const size_t need = sizeof(float) * (2 * S4 + nz + ncay + (a.smem_svd ? 0 : (2 * nb + nv)));
+    const size_t need = sizeof(float) * (S4 + nz + ncay + (a.smem_svd ? 0 : (2 * nb + nv)));
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
     float* s = reinterpret_cast<float*>(ctx->scratch);
-    a.P = s;
-    a.Mp = s + S4;
+    a.Mp = s;
     a.Zg = a.Mp + S4;
     a.Cay = ncay ? a.Zg + nz : nullptr;
     if (!a.smem_svd) {

@@ -21,6 +21,14 @@ constexpr int NW = NT / 32;      // warps per CTA
 constexpr int PMAX = 8;          // largest transform (projective)
 constexpr int MAX_SIDE = 512;
 
+// Advances the (row r, column c) of a column-major pixel index e = c R + r by a stride given as
+// stepc = stride / R whole columns plus stepr = stride % R rows, without a division (r < R).
+__device__ __forceinline__ void next_rc(int& r, int& c, int R, int stepr, int stepc) {
+    r += stepr;
+    c += stepc;
+    if (r >= R) { r -= R; ++c; }
+}
+
 // ------------------------------------------------------------------------------ parameters
 struct Params {
     double lam, eps1, eps2, rho0, mu0, mu_max, eps_svd, outer_tol;
@@ -48,8 +56,8 @@ struct Planes {
     float* A;      // S
     float* E;      // S
     float* Y;      // S   (the scaled multiplier Y~ = W^T Y of Sec. 4.3)
-    float* P;      // S   (W^T W (A + E - D_hat), carried between iterations)
-    float* Mp;     // S   (previous M, for the warm-start gate)
+    float* P;      // S   (work plane: the power iteration's vector of an image set)
+    float* Mp;     // S   (previous M, for the warm-start gate; kept only while the gate is on)
     float* Bg;     // ldb * Cp  (SVD work, global mode only)
     float* Vg;     // ldv * Cp
     float* Tg;     // ldb * Cp

@@ -63,7 +63,6 @@ struct InnerArgs {
     float* A;
     float* E;
     float* Y;
-    float* P;      // scratch S
     float* Mp;     // scratch S
     float* Bg;     // global SVD buffers when !smem_svd
     float* Vg;

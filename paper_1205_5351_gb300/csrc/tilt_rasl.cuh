@@ -179,21 +179,22 @@ __device__ __forceinline__ void col_e_update(const float* __restrict__ A, float*
     }
 }
 
-//   P'' = (A + E - D_hat) - J_c cc;  Y' = Y + mu P'';  M = A - Y' imun - P'' (into T and Mp);
-//   acc += (||P''||^2, ||M - M_prev||^2, ||M||^2)
+//   P'' = (A + E - D_hat) - J_c cc;  Y' = Y + mu P'';  M = A - Y' imun - P'' (into T, and into
+//   Mp while the warm-start gate is on);  acc += (||P''||^2, ||M - M_prev||^2, ||M||^2), the
+//   last two only while the gate is on
 template <int W>
 __device__ __forceinline__ void col_y_update(const float* __restrict__ A, const float* __restrict__ E,
                                              const float* __restrict__ D, float* __restrict__ Y, float* __restrict__ T,
                                              float* __restrict__ Mp, const float* __restrict__ Jc, size_t S, int r0,
                                              int r1, int lane, int p, const float (&cc)[PMAX], float muf, float imun,
-                                             float (&acc)[3]) {
+                                             bool gate, float (&acc)[3]) {
     for (int r = r0 + W * lane; r < r1; r += 32 * W) {
         float a[W], e[W], d[W], y[W], mo[W], jc[W], mv[W];
         ldw<W>(A + r, a);
         ldw<W>(E + r, e);
         ldw<W>(D + r, d);
         ldw<W>(Y + r, y);
-        ldw<W>(Mp + r, mo);
+        if (gate) ldw<W>(Mp + r, mo);
 #pragma unroll
         for (int u = 0; u < W; ++u) jc[u] = 0.f;
 #pragma unroll
@@ -211,12 +212,14 @@ __device__ __forceinline__ void col_y_update(const float* __restrict__ A, const 
             y[u] = fmaf(muf, pp, y[u]);
             acc[0] = fmaf(pp, pp, acc[0]);
             mv[u] = a[u] - y[u] * imun - pp;
-            acc[1] = fmaf(mv[u] - mo[u], mv[u] - mo[u], acc[1]);
-            acc[2] = fmaf(mv[u], mv[u], acc[2]);
+            if (gate) {
+                acc[1] = fmaf(mv[u] - mo[u], mv[u] - mo[u], acc[1]);
+                acc[2] = fmaf(mv[u], mv[u], acc[2]);
+            }
         }
         stw<W>(Y + r, y);
         stw<W>(T + r, mv);
-        stw<W>(Mp + r, mv);
+        if (gate) stw<W>(Mp + r, mv);
     }
 }
 
@@ -444,6 +447,8 @@ static __device__ InnerOut k_inner_rasl(const RaslProblem& pr, const Dims& d, co
     Dims dsvt = d;
     dsvt.p = 0;                       // the SVT step accumulates no J^T products here
     const int R4 = (R % 4 == 0) ? R : 0;   // rows visited four at a time (16-byte accesses)
+    // the previous M (Mp) is kept only for the gate of Algorithm 2 (off when eps_svd < 0)
+    const bool gate = prm.eps_svd >= 0.0;
     InnerOut out;
     out.iters = 0; out.sweeps = 0; out.warm = 0; out.reorth = 0; out.cayley = 0; out.rank = 0;
     out.cancelled = false;
@@ -507,10 +512,12 @@ static __device__ InnerOut k_inner_rasl(const RaslProblem& pr, const Dims& d, co
                 Y[o + r] = y;
                 const float mv = a - y * imu - pp;
                 buf.T[(size_t)c * ldb + r] = mv;
-                const float mo = Mp[o + r];
-                g[0] = fmaf(mv - mo, mv - mo, g[0]);
-                g[1] = fmaf(mv, mv, g[1]);
-                Mp[o + r] = mv;
+                if (gate) {
+                    const float mo = Mp[o + r];
+                    g[0] = fmaf(mv - mo, mv - mo, g[0]);
+                    g[1] = fmaf(mv, mv, g[1]);
+                    Mp[o + r] = mv;
+                }
             }
         }
         block_sum_f<2>(g, sc->red);
@@ -615,8 +622,8 @@ static __device__ InnerOut k_inner_rasl(const RaslProblem& pr, const Dims& d, co
                 float cc[PMAX];
                 rasl_coeffs(row, RC_B2, sc->dtau, p, lane, cc, true);
                 float* Tc = buf.T + (size_t)c * ldb;
-                col_y_update<4>(A + o, E + o, Dhat + o, Y + o, Tc, Mp + o, Jc, S, 0, R4, lane, p, cc, muf, imun, acc);
-                col_y_update<1>(A + o, E + o, Dhat + o, Y + o, Tc, Mp + o, Jc, S, R4, R, lane, p, cc, muf, imun, acc);
+                col_y_update<4>(A + o, E + o, Dhat + o, Y + o, Tc, Mp + o, Jc, S, 0, R4, lane, p, cc, muf, imun, gate, acc);
+                col_y_update<1>(A + o, E + o, Dhat + o, Y + o, Tc, Mp + o, Jc, S, R4, R, lane, p, cc, muf, imun, gate, acc);
             }
             block_sum_f<3>(acc, sc->red);
             if (threadIdx.x == 0) {

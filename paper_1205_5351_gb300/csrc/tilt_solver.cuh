@@ -533,11 +533,16 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
 template <int NCH, bool TCP = true>
 static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam, double mu0, const float* __restrict__ Dhat,
                             const float* __restrict__ J, float* __restrict__ A, float* __restrict__ E,
-                            float* __restrict__ Y, float* __restrict__ P, float* __restrict__ Mp, SvdBufs buf,
+                            float* __restrict__ Y, float* __restrict__ Mp, SvdBufs buf,
                             bool& haveV, const SmemLayout& L, Result* cyc, int jsched, const int* cancel,
                             float* cay = nullptr) {
     Scratch* sc = L.sc;
     const int p = d.p, S = d.S, R = d.R, ldb = d.ldb;
+    // the gate of Algorithm 2 compares M with the previous iteration's M (kept in Mp); with the
+    // gate off (eps_svd < 0) the previous M is neither read nor kept
+    const bool gate = prm.eps_svd >= 0.0;
+    // pixel e = c R + r of a thread's next element: e + NT
+    const int stepr = NT % R, stepc = NT / R;
     bool haveUS = false;              // factors of a previous SVD of this inner loop (Algorithm 2)
     float* cay_ws = (TCP && prm.svd_ws == 1) ? cay : nullptr;
     InnerOut out;
@@ -588,6 +593,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
         }
         const float imu = (float)(1.0 / mu0);
         double g[2] = {0.0, 0.0};
+        int r = threadIdx.x % R, c = threadIdx.x / R;
         for (int e = threadIdx.x; e < S; e += NT) {
             float jc = 0.f, jy = 0.f;
 #pragma unroll
@@ -602,14 +608,15 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             const float y = Y[e] - jy;
             const float pp = (a + E[e] - Dhat[e]) - jc;
             Y[e] = y;
-            P[e] = pp;
             const float mv = a - y * imu - pp;
-            const int r = e % R, c = e / R;
             buf.T[(size_t)c * ldb + r] = mv;
-            const float mo = Mp[e];
-            g[0] += (double)((mv - mo) * (mv - mo));
-            g[1] += (double)(mv * mv);
-            Mp[e] = mv;
+            if (gate) {
+                const float mo = Mp[e];
+                g[0] += (double)((mv - mo) * (mv - mo));
+                g[1] += (double)(mv * mv);
+                Mp[e] = mv;
+            }
+            next_rc(r, c, R, stepr, stepc);
         }
         block_sum64<2>(g, sc->red);
         if (threadIdx.x == 0) { sc->scal[5] = g[0]; sc->scal[6] = g[1]; }
@@ -718,6 +725,7 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
             const float muf = sc->fs[FS_MU];
             const float imun = sc->fs[FS_IMUN];
             float acc[3] = {0.f, 0.f, 0.f};
+            int r = threadIdx.x % R, c = threadIdx.x / R;
             for (int e = threadIdx.x; e < S; e += NT) {
                 float jc = 0.f;
 #pragma unroll
@@ -727,15 +735,16 @@ static __device__ InnerOut k_inner(const Dims& d, const Params& prm, double lam,
                 const float pp = (a + E[e] - Dhat[e]) - jc;
                 const float y = fmaf(muf, pp, Y[e]);
                 Y[e] = y;
-                P[e] = pp;
                 acc[0] = fmaf(pp, pp, acc[0]);
                 const float mv = a - y * imun - pp;
-                const int r = e % R, c = e / R;
                 buf.T[(size_t)c * ldb + r] = mv;
-                const float mo = Mp[e];
-                acc[1] = fmaf(mv - mo, mv - mo, acc[1]);
-                acc[2] = fmaf(mv, mv, acc[2]);
-                Mp[e] = mv;
+                if (gate) {
+                    const float mo = Mp[e];
+                    acc[1] = fmaf(mv - mo, mv - mo, acc[1]);
+                    acc[2] = fmaf(mv, mv, acc[2]);
+                    Mp[e] = mv;
+                }
+                next_rc(r, c, R, stepr, stepc);
             }
             block_sum_f<3>(acc, sc->red);
             if (threadIdx.x == 0) {
@@ -1015,7 +1024,7 @@ static __device__ void solve_problem(const Problem& pr, const SmemLayout& L, Res
             double mu0 = prm.mu0;
             if (!(mu0 > 0.0)) mu0 = 1.25 / spectral_norm(pr.pl.Dhat, d, L.sigma, L.w, sc);
             if (threadIdx.x == 0) res.cyc_other += clk() - t1;
-            InnerOut io = k_inner<NCH, TCP>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y, pr.pl.P,
+            InnerOut io = k_inner<NCH, TCP>(d, prm, lam, mu0, pr.pl.Dhat, pr.pl.J, pr.pl.A, pr.pl.E, pr.pl.Y,
                                   pr.pl.Mp, buf, haveV, L, &res, pr.jsched, pr.cancel, pr.pl.Cay);
             inner_total += io.iters;
             sweeps += io.sweeps;

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(NT, 1) inner_step_kernel(InnerArgs a) {
     __shared__ Result cyc;
     if (threadIdx.x == 0) cyc.cyc_elem = cyc.cyc_svd = cyc.cyc_recon = cyc.cyc_warp = cyc.cyc_other = 0;
     __syncthreads();
-    InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.P, a.Mp, buf, haveV, L, &cyc,
+    InnerOut io = k_inner<4>(d, a.prm, lam, mu0, a.Dhat, a.J, a.A, a.E, a.Y, a.Mp, buf, haveV, L, &cyc,
                              a.jsched, nullptr, a.Cay);
     if (threadIdx.x == 0) {
         a.out->status = io.tc_timeout ? -5 : io.bad ? -1 : 0;

@@ -110,6 +110,34 @@ def test_rasl_inner_loop_parity(T, ctx, nimg, m, n, ttype):
         assert e["rank"][0] == e["rank"][1] and e["obj"] <= 1e-5, e
 
 
+@pytest.mark.parametrize("eps_svd", [0.0, 0.05])
+@pytest.mark.parametrize("nimg,m,n,ttype", [CASES[0], CASES[3]])
+def test_rasl_inner_loop_with_the_warm_start_gate(T, ctx, nimg, m, n, ttype, eps_svd):
+    # the gate of Algorithm 2 on the Jacobi warm start (||M_k - M_k-1|| < eps_svd ||M_k||): with
+    # eps_svd = 0 no SVD is warm-started, with 0.05 those after the first few iterations are;
+    # the SVT is exact either way, so the result is the oracle's at the inner loop's bounds,
+    # E's error measured at the scale of the data (E = T(N) is 1-Lipschitz in N, whose rounding
+    # is at the scale of D_hat; relative to the small ||E|| the cold 48 x 48 sets read 1.1e-4)
+    sets = _sets(1, nimg, m, n, ttype, 300 + nimg)
+    s = sets[0]
+    out = _run(T, ctx, sets, T.default_params(max_outer=1, eps_svd=eps_svd))
+    off = _run(T, ctx, sets, T.default_params(max_outer=1))
+    ref = O.rasl(s.imgs.astype(np.float64), s.tau0, ttype, m, n, O.Params(max_outer=1))
+    r, r_off = out["results"][0], off["results"][0]
+    assert r_off["svd_warm"] == r_off["inner_iters"] - 1, r_off
+    if eps_svd == 0.0:
+        assert r["svd_warm"] == 0, r
+    else:
+        assert 0 < r["svd_warm"] <= r["inner_iters"] - 1, r
+    e = dict(iters=(r["inner_iters"], ref.inner_iters), A=rel(out["A"][0], ref.A), E=rel(out["E"][0], ref.E),
+             E_abs=np.linalg.norm(out["E"][0] - ref.E) / np.linalg.norm(ref.Dhat),
+             dtau=rel(out["tau"][0] - s.tau0, ref.tau - s.tau0), rank=(r["rank"], ref.rank))
+    print("gated inner loop", eps_svd, e, r["svd_warm"], r["svd_sweeps"], r_off["svd_sweeps"])
+    assert abs(e["iters"][0] - e["iters"][1]) <= 1, e
+    assert e["A"] <= 1e-4 and e["E_abs"] <= 1e-4 and e["dtau"] <= 1e-4, e
+    assert e["rank"][0] == e["rank"][1], e
+
+
 def test_rasl_outer_loop_parity(T, ctx):
     # three outer steps: tau within 1e-3 relative of the oracle's (the benchmark spec's bound for
     # transforms), equal rank and outer iterations.  (The displacement tau - tau0 alone, held to
