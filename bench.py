@@ -73,9 +73,9 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partition
 # They hold only for the kernel
 # sources they were taken on: when the SHA-256 of SOLVER_SOURCES (comments removed) differs,
 # traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "1f53afb690d3e8e408659aec4f521a42f1b6c7af2828e79d0a89fcf7ae3f25bc",
-               "bytes": {"affine/1024/0": 2997433600 + 3390507008,
-                         "affine/1024/1": 2403687680 + 2710898688}}
+NCU_TRAFFIC = {"sources_sha256": "1fb83ea6bf2fb3824338336c9988492f71157490b5d37b442d8eaa528897189c",
+               "bytes": {"affine/1024/0": 3900157952 + 3853043456,
+                         "affine/1024/1": 2256609792 + 2625253888}}
 
 
 def strip_c_comments(src: str) -> str:

@@ -659,16 +659,22 @@ static __device__ double spectral_norm(const float* __restrict__ X, const Dims& 
 //
 // Round-robin ordering: each round is a set of disjoint column pairs.  A pair is handled by
 // a group of 8 lanes (4 pairs in flight per warp, 64 per CTA): lane g holds the float4
-// chunks g, g+8, g+16, ... of both columns, so the three dot products need 3 shuffle levels
+// chunks g, g+8, g+16, ... of both columns, so the dot product needs 3 shuffle levels
 // and, when the columns fit in registers (R <= 128), the rotation reuses the loaded values.
 // A pair is rotated when |b_i.b_j| > tol ||b_i|| ||b_j||, in Rutishauser's form
 // x' = x - s (y + r x), y' = y + s (x - r y), r = tan(theta/2), so that small angles do not
 // inflate the column norms (with c rounded to 1 the plain form grows them by t^2/2 per
-// rotation).  Sweeps stop when one rotates nothing, or when the largest rotated cosine is
-// below 32 tol (cyclic Jacobi converges quadratically near the end, so the next sweep would
-// find nothing above tol).  Returns the number of sweeps.
+// rotation).  The squared column norms are carried in a shared array instead of being
+// recomputed at every pair: the rotation that zeroes b_i.b_j = g maps them to
+// ||b_i||^2 - t g and ||b_j||^2 + t g (t = tan(theta)), the updates of Hestenes' method as
+// in LAPACK's xGESVJ; a norm that the update shrinks below a quarter is recomputed from the
+// rotated column (the difference would have cancelled), and every sweep starts from
+// recomputed norms, so rounding cannot accumulate over more than one sweep.  Sweeps stop when
+// one rotates nothing, or when the largest rotated cosine is below sqrt(tol) (cyclic Jacobi
+// converges quadratically near the end, so the next sweep would find nothing above tol).
+// Returns the number of sweeps.
 struct RotParams {
-    float s, r;
+    float s, r, t;
     bool rot;
     float cosabs;
 };
@@ -683,6 +689,7 @@ __device__ inline RotParams rotation_for(float a, float b, float g, float tol) {
     p.cosabs = 0.f;
     p.s = 0.f;
     p.r = 0.f;
+    p.t = 0.f;
     if (p.rot) {
         // square roots as x rsqrt(x): s and r share q, so the applied transform
         // [[1 - s r, -s], [s, 1 - s r]] stays orthogonal to O(t^2 eps) whatever q's rounding
@@ -696,6 +703,7 @@ __device__ inline RotParams rotation_for(float a, float b, float g, float tol) {
         const float q = q2 * rsqrtf(q2);
         p.s = __fdividef(t, q);
         p.r = __fdividef(t, 1.f + q);
+        p.t = t;
     }
     return p;
 }
@@ -722,10 +730,16 @@ __device__ inline float group_sum(float v, unsigned mask, int gw) {
 
 // One pair step of the one-sided Jacobi for columns i, j, executed by a group of gw lanes
 // (lane g of the group holds float4 chunks g, g+gw, ... ; in registers while nqb <= gw NCH).
-template <int NCH, int gw>
-__device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, float4* vj, int nqb, int nqv, int g,
+// TRACK: ni, nj hold the squared norms of the two columns, read and updated here; otherwise
+// (the staged sweeps) the norms are computed from the columns at every pair and ni, nj unused.
+constexpr float NORM_RECOMPUTE = 0.25f;   // recompute a norm that an update shrinks below this fraction
+
+template <int NCH, int gw, bool TRACK = true>
+__device__ inline void jacobi_pair_cols(float4* __restrict__ bi, float4* __restrict__ bj, float4* __restrict__ vi,
+                                        float4* __restrict__ vj, float* ni, float* nj, int nqb, int nqv, int g,
                                         unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
     float a = 0.f, b = 0.f, gg = 0.f;
+    if (TRACK) { a = *ni; b = *nj; }
     if (in_regs) {
         float4 x[NCH], y[NCH];
         float pa[NCH], pb[NCH], pg[NCH];
@@ -739,18 +753,24 @@ __device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, floa
                 x[t] = make_float4(0.f, 0.f, 0.f, 0.f);
                 y[t] = x[t];
             }
-            pa[t] = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, x[t].w * x[t].w)));
-            pb[t] = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, y[t].w * y[t].w)));
+            if (!TRACK) {
+                pa[t] = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, x[t].w * x[t].w)));
+                pb[t] = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, y[t].w * y[t].w)));
+            }
             pg[t] = fmaf(x[t].x, y[t].x, fmaf(x[t].y, y[t].y, fmaf(x[t].z, y[t].z, x[t].w * y[t].w)));
         }
 #pragma unroll
         for (int t = 0; t < NCH; ++t) {
-            a += pa[t];
-            b += pb[t];
+            if (!TRACK) {
+                a += pa[t];
+                b += pb[t];
+            }
             gg += pg[t];
         }
-        a = group_sum(a, gmask, gw);
-        b = group_sum(b, gmask, gw);
+        if (!TRACK) {
+            a = group_sum(a, gmask, gw);
+            b = group_sum(b, gmask, gw);
+        }
         gg = group_sum(gg, gmask, gw);
         const RotParams rp = rotation_for(a, b, gg, tol);
         if (rp.rot) {
@@ -758,9 +778,27 @@ __device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, floa
             for (int t = 0; t < NCH; ++t) {
                 const int q = g + gw * t;
                 if (q < nqb) {
-                    bi[q] = rot_x(x[t], y[t], rp.s, rp.r);
-                    bj[q] = rot_y(x[t], y[t], rp.s, rp.r);
+                    const float4 xn = rot_x(x[t], y[t], rp.s, rp.r);
+                    const float4 yn = rot_y(x[t], y[t], rp.s, rp.r);
+                    bi[q] = xn;
+                    bj[q] = yn;
+                    x[t] = xn;
+                    y[t] = yn;
                 }
+            }
+            if (TRACK) {
+                float na = fmaf(-rp.t, gg, a), nb = fmaf(rp.t, gg, b);
+                if (na < NORM_RECOMPUTE * a || nb < NORM_RECOMPUTE * b) {   // the same in every lane of the group
+                    float sa = 0.f, sb = 0.f;
+#pragma unroll
+                    for (int t = 0; t < NCH; ++t) {
+                        sa = fmaf(x[t].x, x[t].x, fmaf(x[t].y, x[t].y, fmaf(x[t].z, x[t].z, fmaf(x[t].w, x[t].w, sa))));
+                        sb = fmaf(y[t].x, y[t].x, fmaf(y[t].y, y[t].y, fmaf(y[t].z, y[t].z, fmaf(y[t].w, y[t].w, sb))));
+                    }
+                    na = group_sum(sa, gmask, gw);
+                    nb = group_sum(sb, gmask, gw);
+                }
+                if (g == 0) { *ni = na; *nj = nb; }
             }
             // V (C <= R rows): the same chunk pattern, unrolled so that all loads are in flight
 #pragma unroll
@@ -782,12 +820,16 @@ __device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, floa
     } else {
         for (int q = g; q < nqb; q += gw) {
             const float4 x = bi[q], y = bj[q];
-            a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
-            b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
+            if (!TRACK) {
+                a = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, a))));
+                b = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, b))));
+            }
             gg = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, gg))));
         }
-        a = group_sum(a, gmask, gw);
-        b = group_sum(b, gmask, gw);
+        if (!TRACK) {
+            a = group_sum(a, gmask, gw);
+            b = group_sum(b, gmask, gw);
+        }
         gg = group_sum(gg, gmask, gw);
         const RotParams rp = rotation_for(a, b, gg, tol);
         if (rp.rot) {
@@ -795,6 +837,20 @@ __device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, floa
                 const float4 x = bi[q], y = bj[q];
                 bi[q] = rot_x(x, y, rp.s, rp.r);
                 bj[q] = rot_y(x, y, rp.s, rp.r);
+            }
+            if (TRACK) {
+                float na = fmaf(-rp.t, gg, a), nb = fmaf(rp.t, gg, b);
+                if (na < NORM_RECOMPUTE * a || nb < NORM_RECOMPUTE * b) {   // the same in every lane of the group
+                    float sa = 0.f, sb = 0.f;
+                    for (int q = g; q < nqb; q += gw) {      // the chunks this lane has just written
+                        const float4 x = bi[q], y = bj[q];
+                        sa = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, sa))));
+                        sb = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, sb))));
+                    }
+                    na = group_sum(sa, gmask, gw);
+                    nb = group_sum(sb, gmask, gw);
+                }
+                if (g == 0) { *ni = na; *nj = nb; }
             }
             for (int q = g; q < nqv; q += gw) {
                 const float4 x = vi[q], y = vj[q];
@@ -807,14 +863,31 @@ __device__ inline void jacobi_pair_cols(float4* bi, float4* bj, float4* vi, floa
     }
 }
 
-template <int NCH, int gw>
-__device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, int i, int j, int nqb, int nqv, int g,
-                                   unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
-    jacobi_pair_cols<NCH, gw>(reinterpret_cast<float4*>(B + (size_t)i * ldb),
+template <int NCH, int gw, bool TRACK>
+__device__ inline void jacobi_pair(float* B, int ldb, float* V, int ldv, float* nrm, int i, int j, int nqb, int nqv,
+                                   int g, unsigned gmask, float tol, bool in_regs, bool& rotated, float& maxcos) {
+    jacobi_pair_cols<NCH, gw, TRACK>(reinterpret_cast<float4*>(B + (size_t)i * ldb),
                               reinterpret_cast<float4*>(B + (size_t)j * ldb),
                               reinterpret_cast<float4*>(V + (size_t)i * ldv),
-                              reinterpret_cast<float4*>(V + (size_t)j * ldv), nqb, nqv, g, gmask, tol, in_regs,
-                              rotated, maxcos);
+                              reinterpret_cast<float4*>(V + (size_t)j * ldv), nrm + i, nrm + j, nqb, nqv, g, gmask,
+                              tol, in_regs, rotated, maxcos);
+}
+
+// Squared norms of the C columns of B (one warp per column), for the start of a sweep; the
+// caller's next barrier publishes them.
+__device__ inline void column_norms(const float* B, int ldb, int C, float* nrm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nqb = ldb / 4;
+    for (int c = warp; c < C; c += NW) {
+        const float4* col = reinterpret_cast<const float4*>(B + (size_t)c * ldb);
+        float s = 0.f;
+        for (int q = lane; q < nqb; q += 32) {
+            const float4 x = col[q];
+            s = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, s))));
+        }
+        s = warp_sum(s);
+        if (lane == 0) nrm[c] = s;
+    }
 }
 
 // End of a sweep: did any pair rotate, and the largest rotated cosine (all threads).
@@ -843,9 +916,9 @@ __device__ inline bool sweep_done(bool rotated, float maxcos, float tol, int* fl
 // barrier after each block round.  Both visit every pair once per sweep.
 // The group width is a template parameter: the shuffle widths and chunk indices sit on the
 // critical path of every pair step.
-template <int NCH, int gw>
+template <int NCH, int gw, bool TRACK>
 static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                                  int* flag, int order) {
+                                  int* flag, int order, float* nrm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane & (gw - 1);
     const unsigned gmask = (gw == 32 ? 0xFFFFFFFFu : ((1u << gw) - 1u)) << (lane & ~(gw - 1));
@@ -859,6 +932,7 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
         const int npairs = Ce / 2;
         const int nr = Ce - 1;
         while (sweep < max_sweeps) {
+            if (TRACK) column_norms(B, ldb, C, nrm);
             if (threadIdx.x == 0) { flag[0] = 0; reinterpret_cast<float*>(flag)[1] = 0.f; }
             __syncthreads();
             bool rotated = false;
@@ -871,7 +945,7 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
                     if (j >= nr) j -= nr;
                     j += 1;
                     if (i >= C || j >= C) continue;
-                    jacobi_pair<NCH, gw>(B, ldb, V, ldv, i, j, nqb, nqv, g, gmask, tol, in_regs, rotated, maxcos);
+                    jacobi_pair<NCH, gw, TRACK>(B, ldb, V, ldv, nrm, i, j, nqb, nqv, g, gmask, tol, in_regs, rotated, maxcos);
                 }
                 __syncthreads();
             }
@@ -891,6 +965,7 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
     const int nbr = NB - 1;                        // block rounds per sweep
     const int nwu = NB / 2;                        // warps with a block pair
     while (sweep < max_sweeps) {
+        if (TRACK) column_norms(B, ldb, C, nrm);
         if (threadIdx.x == 0) { flag[0] = 0; reinterpret_cast<float*>(flag)[1] = 0.f; }
         __syncthreads();
         bool rotated = false;
@@ -915,7 +990,7 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
                             lj += 1;
                             const int ci = blk * b + li, cj = blk * b + lj;
                             if (ci < C && cj < C)
-                                jacobi_pair<NCH, gw>(B, ldb, V, ldv, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
+                                jacobi_pair<NCH, gw, TRACK>(B, ldb, V, ldv, nrm, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
                                                      rotated, maxcos);
                         }
                         __syncwarp();
@@ -927,7 +1002,7 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
                         if (c >= b) c -= b;
                         const int ci = P * b + a, cj = Q * b + c;
                         if (ci < C && cj < C)
-                            jacobi_pair<NCH, gw>(B, ldb, V, ldv, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
+                            jacobi_pair<NCH, gw, TRACK>(B, ldb, V, ldv, nrm, ci, cj, nqb, nqv, g, gmask, tol, in_regs,
                                                  rotated, maxcos);
                     }
                     __syncwarp();
@@ -1019,8 +1094,8 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
                     if (lj >= b - 1) lj -= b - 1;
                     lj += 1;
                     if (li < nP && lj < nP)
-                        jacobi_pair_cols<NCH, 32>(colB(li), colB(lj), colV(li), colV(lj), nqb, nqv, lane, 0xFFFFFFFFu,
-                                                  tol, in_regs, rotated, maxcos);
+                        jacobi_pair_cols<NCH, 32, false>(colB(li), colB(lj), colV(li), colV(lj), nullptr, nullptr, nqb,
+                                                         nqv, lane, 0xFFFFFFFFu, tol, in_regs, rotated, maxcos);
                 }
                 __syncthreads();
             }
@@ -1037,8 +1112,9 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
                         int c = a + s;
                         if (c >= b) c -= b;
                         if (a < nP && c < nQ)
-                            jacobi_pair_cols<NCH, 32>(colB(a), colB(cur + c), colV(a), colV(cur + c), nqb, nqv, lane,
-                                                      0xFFFFFFFFu, tol, in_regs, rotated, maxcos);
+                            jacobi_pair_cols<NCH, 32, false>(colB(a), colB(cur + c), colV(a), colV(cur + c), nullptr,
+                                                             nullptr, nqb, nqv, lane, 0xFFFFFFFFu, tol, in_regs, rotated,
+                                                             maxcos);
                     }
                     __syncthreads();
                 }
@@ -1083,13 +1159,16 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
     return sweep;
 }
 
-template <int NCH>
+// TRACK: carry the squared column norms in nrm (C floats of shared memory) instead of
+// recomputing them at every pair; columns of one float4 chunk per lane (the 32 x 32
+// factor of the QR path) gain nothing from it and run with TRACK = false (nrm unused).
+template <int NCH, bool TRACK = true>
 static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                                int* flag, int gw, int order) {
+                                int* flag, int gw, int order, float* nrm) {
     if (C < 2) return 0;
-    if (gw == 4) return k2_jacobi_w<NCH, 4>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
-    if (gw == 16) return k2_jacobi_w<NCH, 16>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
-    return k2_jacobi_w<NCH, 8>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order);
+    if (gw == 4) return k2_jacobi_w<NCH, 4, TRACK>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order, nrm);
+    if (gw == 16) return k2_jacobi_w<NCH, 16, TRACK>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order, nrm);
+    return k2_jacobi_w<NCH, 8, TRACK>(B, ldb, V, ldv, R, C, tol, max_sweeps, flag, order, nrm);
 }
 
 // Default group width for a C-column matrix: every pair of a round in flight at once when

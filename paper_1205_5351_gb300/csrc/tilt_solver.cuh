@@ -168,8 +168,8 @@ static __device__ SvtStepOut svt_tall_qr(const Dims& d, SvdBufs& buf, const Smem
     __syncthreads();
     so.warm = warm;
     const int js = default_schedule(C, C);
-    so.sweeps = k2_jacobi<NCH>(Bc, Cp, buf.V, ldv, C, C, jacobi_tol(C), warm ? 30 : 40, sc->flag, jsched_width(js),
-                               jsched_order(js));
+    so.sweeps = k2_jacobi<NCH, false>(Bc, Cp, buf.V, ldv, C, C, jacobi_tol(C), warm ? 30 : 40, sc->flag,
+                                      jsched_width(js), jsched_order(js), nullptr);
     haveV = true;
     svt_weights(Bc, Cp, C, C, eps, L.sigma, L.w, L.kept, sc);
     so.t_svd_end = clk();
@@ -431,7 +431,7 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
         }
     } else {
         so.sweeps = k2_jacobi<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
-                                   jsched_width(jsched), jsched_order(jsched));
+                                   jsched_width(jsched), jsched_order(jsched), L.w);
     }
     haveV = true;
     svt_weights(buf.B, ldb, R, C, eps, L.sigma, L.w, L.kept, sc);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
                                  reinterpret_cast<float*>(stage), &L.sc->tc);
     } else {
         sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag, jsched_width(a.jsched),
-                          jsched_order(a.jsched));
+                          jsched_order(a.jsched), L.w);
     }
     if (sw < 0) {
         if (threadIdx.x == 0) a.out->status = -5;
