@@ -73,9 +73,9 @@ FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell SM: 4 partition
 # They hold only for the kernel
 # sources they were taken on: when the SHA-256 of SOLVER_SOURCES (comments removed) differs,
 # traffic is null.
-NCU_TRAFFIC = {"sources_sha256": "1fb83ea6bf2fb3824338336c9988492f71157490b5d37b442d8eaa528897189c",
-               "bytes": {"affine/1024/0": 3900157952 + 3853043456,
-                         "affine/1024/1": 2256609792 + 2625253888}}
+NCU_TRAFFIC = {"sources_sha256": "abfb8dac565e016654114011f19ae85959d83db5d65a7d331898a2a3ff5f82a3",
+               "bytes": {"affine/1024/0": 3881995776 + 3850514688,
+                         "affine/1024/1": 2256996864 + 2622205952}}
 
 
 def strip_c_comments(src: str) -> str:

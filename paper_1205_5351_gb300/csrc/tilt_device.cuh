@@ -731,7 +731,7 @@ __device__ inline float group_sum(float v, unsigned mask, int gw) {
 // One pair step of the one-sided Jacobi for columns i, j, executed by a group of gw lanes
 // (lane g of the group holds float4 chunks g, g+gw, ... ; in registers while nqb <= gw NCH).
 // TRACK: ni, nj hold the squared norms of the two columns, read and updated here; otherwise
-// (the staged sweeps) the norms are computed from the columns at every pair and ni, nj unused.
+// the norms are computed from the columns at every pair and ni, nj are unused.
 constexpr float NORM_RECOMPUTE = 0.25f;   // recompute a norm that an update shrinks below this fraction
 
 template <int NCH, int gw, bool TRACK = true>
@@ -1024,12 +1024,14 @@ static __device__ int k2_jacobi_w(float* B, int ldb, float* V, int ldv, int R, i
 // thread 0); Q alternates between two buffers, so the write-back of one block overlaps the
 // work on the next.  Inside a block pair one warp rotates one column pair (32 lanes, float4
 // chunks), b disjoint pairs per sub-round and a CTA barrier between sub-rounds, so the
-// sweep reads each column of Q once per row instead of once per pair.  stage: 3 b (ldb + ldv)
-// floats; st: the bulk-copy mbarrier.  Returns the number of sweeps, or -1 when a bounded
+// sweep reads each column of Q once per row instead of once per pair.  The squared norms of
+// the staged columns are computed when a block arrives and carried through its pair steps (nrm:
+// 3 b floats of shared memory, one per stage slot).  stage: 3 b (ldb + ldv) floats; st: the
+// bulk-copy mbarrier.  Returns the number of sweeps, or -1 when a bounded
 // wait for a copy gave up (st->error is set).
 template <int NCH>
 static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
-                                       int* flag, int b, float* stage, TcState* st) {
+                                       int* flag, int b, float* stage, TcState* st, float* nrm) {
     (void)R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int NB = (C + b - 1) / b;
@@ -1086,6 +1088,8 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
             if (!(ok = wait_loads())) break;
             // pairs inside block P: round-robin over b columns, b - 1 sub-rounds of b/2 pairs
             const int nP = ncols(P);
+            column_norms(sB, ldb, nP, nrm);
+            __syncthreads();
             for (int sr = 0; sr < b - 1; ++sr) {
                 if (warp < b / 2) {
                     int li = 0;
@@ -1094,14 +1098,16 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
                     if (lj >= b - 1) lj -= b - 1;
                     lj += 1;
                     if (li < nP && lj < nP)
-                        jacobi_pair_cols<NCH, 32, false>(colB(li), colB(lj), colV(li), colV(lj), nullptr, nullptr, nqb,
-                                                         nqv, lane, 0xFFFFFFFFu, tol, in_regs, rotated, maxcos);
+                        jacobi_pair_cols<NCH, 32, true>(colB(li), colB(lj), colV(li), colV(lj), nrm + li, nrm + lj, nqb,
+                                                        nqv, lane, 0xFFFFFFFFu, tol, in_regs, rotated, maxcos);
                 }
                 __syncthreads();
             }
             if (P + 1 < NB) {
                 if (threadIdx.x == 0) load(P + 1, b);
                 if (!(ok = wait_loads())) break;
+                column_norms(sB + (size_t)b * ldb, ldb, ncols(P + 1), nrm + b);
+                __syncthreads();
             }
             int cur = b;                      // slot base of the buffer holding Q
             for (int Q = P + 1; Q < NB; ++Q) {
@@ -1112,9 +1118,9 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
                         int c = a + s;
                         if (c >= b) c -= b;
                         if (a < nP && c < nQ)
-                            jacobi_pair_cols<NCH, 32, false>(colB(a), colB(cur + c), colV(a), colV(cur + c), nullptr,
-                                                             nullptr, nqb, nqv, lane, 0xFFFFFFFFu, tol, in_regs, rotated,
-                                                             maxcos);
+                            jacobi_pair_cols<NCH, 32, true>(colB(a), colB(cur + c), colV(a), colV(cur + c), nrm + a,
+                                                            nrm + cur + c, nqb, nqv, lane, 0xFFFFFFFFu, tol, in_regs,
+                                                            rotated, maxcos);
                     }
                     __syncthreads();
                 }
@@ -1128,7 +1134,11 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
                         load(Q + 1, other);
                     }
                 }
-                if (Q + 1 < NB && !(ok = wait_loads())) break;
+                if (Q + 1 < NB) {
+                    if (!(ok = wait_loads())) break;
+                    column_norms(sB + (size_t)other * ldb, ldb, ncols(Q + 1), nrm + other);
+                    __syncthreads();
+                }
                 cur = other;
             }
             if (!ok) break;
@@ -1162,6 +1172,7 @@ static __device__ int k2_jacobi_staged(float* B, int ldb, float* V, int ldv, int
 // TRACK: carry the squared column norms in nrm (C floats of shared memory) instead of
 // recomputing them at every pair; columns of one float4 chunk per lane (the 32 x 32
 // factor of the QR path) gain nothing from it and run with TRACK = false (nrm unused).
+// (The staged sweeps carry the norms of their stage slots the same way.)
 template <int NCH, bool TRACK = true>
 static __device__ int k2_jacobi(float* B, int ldb, float* V, int ldv, int R, int C, float tol, int max_sweeps,
                                 int* flag, int gw, int order, float* nrm) {

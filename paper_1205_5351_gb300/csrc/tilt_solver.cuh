@@ -422,7 +422,7 @@ static __device__ __forceinline__ SvtStepOut svt_into(const Dims& d, SvdBufs& bu
     so.warm = warm;
     if (TCP && jsched_order(jsched) == 2) {
         so.sweeps = k2_jacobi_staged<NCH>(buf.B, ldb, buf.V, ldv, R, C, jacobi_tol(R), warm ? 30 : 40, sc->flag,
-                                          jsched_width(jsched), reinterpret_cast<float*>(buf.stage), &sc->tc);
+                                          jsched_width(jsched), reinterpret_cast<float*>(buf.stage), &sc->tc, L.w);
         if (so.sweeps < 0) {
             so.sweeps = 0;
             so.tc_timeout = true;

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT, 1) svt_step_kernel(SvtArgs a) {
     int sw;
     if (jsched_order(a.jsched) == 2) {
         sw = k2_jacobi_staged<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag, jsched_width(a.jsched),
-                                 reinterpret_cast<float*>(stage), &L.sc->tc);
+                                 reinterpret_cast<float*>(stage), &L.sc->tc, L.w);
     } else {
         sw = k2_jacobi<4>(B, d.ldb, V, d.ldv, d.R, d.C, jacobi_tol(d.R), 60, L.sc->flag, jsched_width(a.jsched),
                           jsched_order(a.jsched), L.w);
