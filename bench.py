@@ -256,14 +256,15 @@ def algorithmic_flops(p, r) -> float:
 def phase_work(p, r):
     """Algorithmic work of one solve by phase, from its counters: bytes of the warp/Jacobian
     pass (per outer step: 4 texels read, D_hat and p Jacobian planes written and read back),
-    bytes of the elementwise passes (per inner iteration: A, E, Y, D_hat, P read, J read
-    twice, E, Y, P, M written), FP32 flops of the SVD (Jacobi sweeps and warm-start
-    products) and of the SVT reconstruction (coefficients and product, 2 R C nk each with nk
-    at most C: counted at the kept count's upper bound C / 2, the median measured on these
-    workloads)."""
+    bytes of the elementwise passes (per inner iteration: A, E, Y, D_hat read, J read twice
+    -- the E step's J^T E' is needed before the Y step -- and E, Y, M written; the previous M
+    only while the gate of Algorithm 2 is on, which it is not on these workloads), FP32 flops
+    of the SVD (Jacobi sweeps and warm-start products) and of the SVT reconstruction
+    (coefficients and product, 2 R C nk each with nk at most C: counted at the kept count's
+    upper bound C / 2, the median measured on these workloads)."""
     R, C, S, pp = max(p.m, p.n), min(p.m, p.n), p.m * p.n, p.ttype
     return {"warp_jacobian": r["outer_iters"] * 4.0 * (4 * S + 2 * (1 + pp) * S),
-            "elementwise": r["inner_iters"] * 4.0 * (9 * S + 2 * pp * S),
+            "elementwise": r["inner_iters"] * 4.0 * (7 * S + 2 * pp * S),
             "svd": algorithmic_flops(p, r),
             "svt_reconstruct": r["inner_iters"] * 2 * (2.0 * R * C * (C / 2))}
 
